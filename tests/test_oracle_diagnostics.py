@@ -1,0 +1,132 @@
+"""Pins of the oracle's diagnostics: the spectrum against a brute-force DFT,
+Parseval and single Fourier modes; the exact integer shell rule; structure
+functions and flatness against closed forms (sine wave, Gaussian field);
+domain statistics and derived scales against closed forms."""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import diagnostics as dg
+from oracle import fields
+
+
+def _brute_spectrum(u):
+    _, nz, ny, nx = u.shape
+    n = nx * ny * nz
+    s_max = dg.max_shell(nx, ny, nz)
+    E = np.zeros(s_max + 1)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    for kz in dg.wavenumbers(nz):
+        for ky in dg.wavenumbers(ny):
+            for kx in dg.wavenumbers(nx):
+                ph = np.exp(-2j * np.pi * (kx * x / nx + ky * y / ny + kz * z / nz))
+                e = sum(abs(np.sum(u[d] * ph) / n) ** 2 for d in range(3))
+                K2 = kx * kx + ky * ky + kz * kz
+                s = int(math.floor(math.sqrt(K2) + 0.5))
+                E[s] += 0.5 * e
+    return E
+
+
+def test_spectrum_matches_bruteforce_dft():
+    rng = np.random.default_rng(0)
+    u = rng.normal(size=(3, 4, 5, 6))
+    assert np.allclose(dg.spectrum(u), _brute_spectrum(u), rtol=1e-12, atol=1e-14)
+
+
+def test_spectrum_parseval():
+    rng = np.random.default_rng(1)
+    u = rng.normal(size=(3, 8, 8, 8))
+    E = dg.spectrum(u)
+    assert math.isclose(E.sum(), 0.5 * np.mean(np.sum(u * u, axis=0)), rel_tol=1e-12)
+
+
+def test_spectrum_single_mode():
+    """u_x = A cos(2 pi k.x/N) with k = (1, 2, 2): |k| = 3, E(3) = A^2/4, 0 elsewhere."""
+    n, A = 12, 0.3
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    u = np.zeros((3, n, n, n))
+    u[0] = A * np.cos(2 * np.pi * (1 * x + 2 * y + 2 * z) / n)
+    E = dg.spectrum(u)
+    assert math.isclose(E[3], A * A / 4, rel_tol=1e-12)
+    assert np.abs(np.delete(E, 3)).max() < 1e-25
+
+
+def test_shell_rule_exact():
+    """s - 1/2 <= sqrt(K) < s + 1/2 decided in exact rational arithmetic."""
+    K = np.arange(0, 200000)
+    s = dg.shell_index(K)
+    for k2 in list(range(0, 3000)) + list(range(199000, 200000)):
+        sk = int(s[k2])
+        # (s - 1/2)^2 <= K < (s + 1/2)^2
+        assert Fraction(2 * sk - 1, 2) ** 2 <= k2 or sk == 0
+        assert k2 < Fraction(2 * sk + 1, 2) ** 2
+
+
+def test_sine_wave_structure_functions():
+    """u_x = A sin(2 pi x / N): over full periods <d^2> = A^2 (1 - cos(2 pi r/N))
+    on the x axis and F4 = 3/2; pooled with the zero y, z components S2 is a third."""
+    n, A = 16, 0.2
+    u = np.zeros((3, n, n, n))
+    x = np.arange(n)
+    u[0] = A * np.sin(2 * np.pi * x / n)[None, None, :]
+    sf = dg.structure_functions(u, rs=[1, 2, 3, 5])
+    for i, r in enumerate(sf["r"]):
+        assert math.isclose(sf["S"][i, 2], A * A * (1 - math.cos(2 * math.pi * r / n)) / 3, rel_tol=1e-12)
+        assert abs(sf["S"][i, 1]) < 1e-16
+        assert abs(sf["S"][i, 3]) < 1e-16
+        # pooled: S4 / S2^2 = (3/8 * 16 sin^4 / 3) / (2 sin^2 / 3)^2 -> 3 * 3/2
+        assert math.isclose(sf["F4"][i], 4.5, rel_tol=1e-12)
+
+
+def test_gaussian_field_flatness():
+    """Independent Gaussian velocities: increments are Gaussian, F4 = 3."""
+    rng = np.random.default_rng(7)
+    u = rng.normal(size=(3, 48, 48, 48))
+    sf = dg.structure_functions(u, rs=[1, 4, 8])
+    assert np.all(np.abs(sf["F4"] - 3.0) < 0.05)
+
+
+def test_separations():
+    assert dg.separations(32) == [1, 2, 3, 4, 6, 8, 12, 16]
+    assert dg.separations(100) == [1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48]
+    assert dg.separations(2) == [1]
+
+
+def test_domain_stats_tgv3d():
+    """3-D Taylor-Green: <u.u> = u0^2 / 4, so E_k = u0^2 / 8."""
+    n, u0 = 8, 0.05
+    u = fields.tgv3d(n, n, n, u0)
+    fl = {"drho": np.zeros((n, n, n)), "u": u, "snorm": np.zeros((n, n, n)),
+          "theta": np.full((n, n, n), 0.03)}
+    st = dg.domain_stats(fl, np.zeros_like(u), 0.01, 0.1)
+    assert math.isclose(st["E_k"], u0 * u0 / 8, rel_tol=1e-12)
+    assert math.isclose(st["Kt_mean"], math.sqrt(3) * 0.03, rel_tol=1e-12)
+    assert st["theta_var"] < 1e-30
+    assert st["hist"].sum() == n ** 3
+
+
+def test_derived_scales_single_shell():
+    n, nu0 = 64, 0.01
+    E = np.zeros(20)
+    E[4] = 2e-3
+    d = dg.derived_scales(E, n, nu0, E_k=2e-3)
+    k = 2 * math.pi * 4 / n
+    assert math.isclose(d["L"], 0.75 * math.pi / k, rel_tol=1e-12)
+    assert math.isclose(d["eps"], 2 * nu0 * k * k * 2e-3, rel_tol=1e-12)
+    assert math.isclose(d["u_rms"], math.sqrt(2 * 2e-3 / 3), rel_tol=1e-12)
+    assert math.isclose(d["eta"], (nu0 ** 3 / d["eps"]) ** 0.25, rel_tol=1e-12)
+    # lambda^2 = 15 nu u_rms^2 / eps = 15 * (2/3) E / (2 k^2 E) = 5 / k^2
+    assert math.isclose(d["lambda"], math.sqrt(5) / k, rel_tol=1e-12)
+
+
+def test_oracle_fields_velocity_is_guo_corrected():
+    """u = (sum f c + F/2) / rho (Eq. guo_velocity) in the oracle's fields."""
+    n, F0 = 6, 1e-3
+    L = oracle.OracleLBM(n, n, n, 0.01, 0.0, oracle.FORCE_PAPER_SIN, F0=F0)
+    L.init_equilibrium(np.zeros((3, n, n, n)))
+    u = L.fields()["u"]
+    F = L.force_field()
+    assert np.allclose(u, 0.5 * F, atol=1e-18)
