@@ -1,0 +1,366 @@
+"""Benchmark of the GB300 MRT-Smagorinsky LBM step (one JSON line on stdout).
+
+Workload (headline): the forced-HIT DNS shape, an 800^3 periodic lattice
+(5.12e8 cells) with FP32 storage, seeded random solenoidal initial field
+(k^4 exp(-2 (k/4)^2), u_rms = 0.05), the paper's sinusoidal forcing with
+U0 = 0.043, Cf = 0.2 (F0 = 4.6225e-7), C = 0 and nu0 from Re = 2e4
+(nu0 = 0.00172).  A step is one launch of the fused stream + collide kernel
+over all cells; MLUPS = cells x steps / time.  Extra entries: the same lattice
+with FP16 and BF16 weight-shifted storage, and the 100^3 LES (C = 0.13,
+nu0 = 2.15e-4, FP32).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs as torchrun ranks, one independent lattice per GPU (replicas: the
+method has no exchange step on one box), value = total cell updates of all
+ranks / max rank time.  --impl reference times the FP64 CPU oracle on a
+bounded 128^3 sample of the same setup on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_UPDATE = {0: 152, 1: 76, 2: 76}  # 19 loads + 19 stores of one stored population
+DTYPE_NAME = {0: "f32", 1: "f32 (f16 storage)", 2: "f32 (bf16 storage)"}
+U0, CF, RE = 0.043, 0.2, 2.0e4
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d.get("hbm_gbs", 6750.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_per_update(kernel_digest: str):
+    """DRAM bytes per cell update of the step kernel from the committed ncu summary,
+    or None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as fh:
+        for ln in fh:
+            if ":" in ln and not ln.startswith("#"):
+                k, v = ln.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("kernel_digest") != kernel_digest:
+        return None
+    key = "dram_bytes_per_update_fp32"
+    return float(vals[key]) if key in vals else None
+
+
+def kernel_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2512_23116_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"lbm_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for ln in fh:
+                parts = [p.strip() for p in ln.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_mlups(n: int, seconds: float, nu0: float, C: float):
+    """The FP64 CPU oracle as it stands, on an n^3 sample, for ~`seconds`."""
+    import oracle
+    import synthetic
+    oracle.build()
+    u = synthetic.random_solenoidal(n, seed=1, urms=0.05)
+    F0 = oracle.forcing_amplitude(CF, U0, n)
+    L = oracle.OracleLBM(n, n, n, nu0, C, oracle.FORCE_PAPER_SIN, F0=F0)
+    L.init_equilibrium(u)
+    L.step(1)
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        L.step(1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return n ** 3 * steps / dt / 1e6, steps, dt
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    n = 128
+    nu0 = U0 * n / RE
+    import oracle
+    import synthetic
+    oracle.build()
+    u = synthetic.random_solenoidal(n, seed=1, urms=0.05)
+    L = oracle.OracleLBM(n, n, n, nu0, 0.0, oracle.FORCE_PAPER_SIN, F0=oracle.forcing_amplitude(CF, U0, n))
+    L.init_equilibrium(u)
+    L.step(args.warmup)
+    t0 = time.perf_counter()
+    L.step(args.steps)
+    dt = time.perf_counter() - t0
+    value = n ** 3 * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": "MLUPS (stream+collide, D3Q19 MRT-Smagorinsky-Guo)",
+        "value": value, "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"forced-HIT DNS shape (800^3 setup), bounded {n}^3 sample for the FP64 CPU oracle",
+                   "cells": n ** 3, "C": 0.0, "nu0": nu0, "Re": RE},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": host_cores(), "kind": "oracle",
+                         "sample": f"{n}^3, {args.steps} steps after {args.warmup} warm-up"},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def make_velocity(n, device):
+    import synthetic
+    k, a = synthetic.spectrum_coefficients(n, n, n, seed=1, k0=4.0, urms=0.05)
+    return synthetic.synthesize_torch(k, a, n, n, n, device, zchunk=32)
+
+
+def time_steps(lbm, lat, stream, steps, warmup, dist):
+    import torch
+    lat.step(warmup)
+    lat.sync()
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    if dist:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    start.record(stream)
+    lat.step(steps)
+    stop.record(stream)
+    stop.synchronize()
+    torch.cuda.synchronize()
+    if dist:
+        torch.distributed.barrier()
+    ms = start.elapsed_time(stop)
+    return ms
+
+
+def run_case(lbm, n, precision, C, nu0, steps, warmup, device, stream, u_dev, dist, clocks=None):
+    """Create, initialise from the device velocity, time `steps` steps."""
+    p = lbm.make_params(n, precision=precision, nu0=nu0, cs=C, f0=CF * U0 * U0 / n,
+                        force_mode=lbm.LBM_FORCE_PAPER_SIN, device=device, stream=stream.cuda_stream)
+    lat = lbm.Lattice(p)
+    lat.init(lbm.LBM_INIT_VELOCITY, u=u_dev)
+    if clocks is not None:
+        with clocks:
+            ms = time_steps(lbm, lat, stream, steps, warmup, dist)
+    else:
+        ms = time_steps(lbm, lat, stream, steps, warmup, dist)
+    cfg = lat.config()
+    st = lat.stats()
+    return lat, ms, cfg, st
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=800)
+    ap.add_argument("--les-n", type=int, default=100)
+    ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world, rank, local = dist_env()
+    dist = world > 1
+    if dist:
+        torch.distributed.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2512_23116_gb300 as lbm
+    lbm.load()
+
+    n = args.n
+    nu0 = U0 * n / RE
+    stream = torch.cuda.Stream(device=dev)
+    u_dev = make_velocity(n, dev)
+    torch.cuda.synchronize()
+    cells = n ** 3
+    clocks = ClockSampler(local)
+    lat, ms, cfg, st = run_case(lbm, n, 0, 0.0, nu0, args.steps, args.warmup, local, stream, u_dev,
+                                dist, clocks)
+    assert math.isfinite(st["E_k"]) and st["cells"] == cells, st
+    # e2e: the public API with host buffers: H2D of the initial field from pinned
+    # memory, the K steps, and the D2H statistics read, all inside the timed region
+    u_host = u_dev.cpu().pin_memory()
+    torch.cuda.synchronize()
+    if dist:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    lbm.lbm_init_field(lat.h, 0, lbm.LBM_INIT_VELOCITY, 0.0, u_host.numpy())
+    lat.step(args.steps)
+    st2 = lat.stats()
+    t_e2e = time.perf_counter() - t0
+    if dist:
+        torch.distributed.barrier()
+    assert math.isfinite(st2["E_k"])
+    lat.close()
+    del u_host
+
+    ms_t = torch.tensor([ms, t_e2e * 1e3], dtype=torch.float64, device=dev)
+    if dist:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms_max, e2e_ms = float(ms_t[0]), float(ms_t[1])
+    value = world * cells * args.steps / (ms_max * 1e-3) / 1e6
+    e2e_value = world * cells * args.steps / (e2e_ms * 1e-3) / 1e6
+
+    hbm_peak, peak_kind = measured_peaks()
+    achieved = cells * BYTES_PER_UPDATE[0] * args.steps / (ms * 1e-3) / 1e9  # this rank's kernel
+    digest = kernel_digest()
+    tpu = traffic_per_update(digest)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "peak_kind": peak_kind,
+                "traffic": None if tpu is None else tpu * cells,
+                "algorithmic_bytes_per_launch": cells * BYTES_PER_UPDATE[0]}
+
+    extra = {}
+    if not args.no_extra:
+        for prec, name in ((1, "fp16_shifted"), (2, "bf16_shifted")):
+            lat2, ms2, cfg2, st3 = run_case(lbm, n, prec, 0.0, nu0, args.steps, args.warmup, local,
+                                            stream, u_dev, dist)
+            lat2.close()
+            extra[f"{n}^3_{name}"] = {
+                "MLUPS": cells * args.steps / (ms2 * 1e-3) / 1e6, "ms_per_step": ms2 / args.steps,
+                "GB_s": cells * BYTES_PER_UPDATE[prec] * args.steps / (ms2 * 1e-3) / 1e9,
+                "frac_hbm": cells * BYTES_PER_UPDATE[prec] * args.steps / (ms2 * 1e-3) / 1e9 / hbm_peak,
+                "speedup_vs_fp32": ms / ms2, "kernel": cfg2}
+        del u_dev
+        torch.cuda.empty_cache()
+        m = args.les_n
+        u_les = make_velocity(m, dev)
+        nu_les = U0 * m / RE
+        lat3, ms3, cfg3, st4 = run_case(lbm, m, 0, 0.13, nu_les, 400, 20, local, stream, u_les, dist)
+        lat3.close()
+        extra[f"{m}^3_les_fp32"] = {
+            "MLUPS": m ** 3 * 400 / (ms3 * 1e-3) / 1e6, "ms_per_step": ms3 / 400,
+            "GB_s": m ** 3 * 152 * 400 / (ms3 * 1e-3) / 1e9, "steps": 400, "C": 0.13, "nu0": nu_les,
+            "note": "76 MB lattice: L2-resident (129 MB L2), not an HBM roofline number",
+            "kernel": cfg3, "theta_mean": st4["theta_mean"]}
+
+    cpu = None
+    if rank == 0:
+        mlups, csteps, cdt = oracle_mlups(64, args.cpu_seconds, U0 * 64 / RE, 0.0)
+        cpu = {"value": mlups, "unit": "MLUPS", "cores": host_cores(), "kind": "oracle",
+               "sample": f"64^3 sample of the same setup (Re = 2e4 at N = 64), {csteps} steps, {cdt:.1f} s"}
+
+    if rank == 0:
+        h2d = 3 * cells * 8
+        line = {
+            "metric": "MLUPS (stream+collide, D3Q19 MRT-Smagorinsky-Guo)",
+            "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"forced-HIT DNS shape {n}^3 FP32 storage, C = 0, Re = 2e4",
+                       "cells_per_gpu": cells, "nu0": nu0, "F0": CF * U0 * U0 / n,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (38.9 GB lattice), no flush",
+                       "kernel": cfg},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d / args.steps,
+                    "d2h_bytes_per_step": 1024.0 / args.steps,
+                    "note": "lbm_init_field from pinned host FP64 velocity + lbm_step(K) + lbm_stats"},
+            "gpu_launches": args.steps,
+            "clocks": clocks.summary(),
+            "extra": extra,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

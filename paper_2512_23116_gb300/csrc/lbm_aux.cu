@@ -1,0 +1,349 @@
+// Auxiliary kernels: initial equilibrium, canonical population access in the
+// AA layout, parity re-layout, the FP64 reduction finisher, the shell binning
+// of the energy spectrum and the structure-function reductions.
+#include <cuda_runtime.h>
+
+#include <cfloat>
+
+#include "lbm_device.cuh"
+#include "lbm_kernels.h"
+
+namespace lbm {
+
+namespace {
+
+constexpr int kAuxThreads = 256;
+
+__device__ __forceinline__ void cell_xyz(int64_t c, int nx, int ny, int& x, int& y, int& z) {
+  const int64_t row = c / nx;
+  x = (int)(c - row * nx);
+  z = (int)(row / ny);
+  y = (int)(row - (int64_t)z * ny);
+}
+
+// Where canonical population a of cell (x, y, z) lives at the given parity:
+// even time: slot a of x; odd time: slot opp(a) of x - c_a.
+__device__ __forceinline__ int64_t canon_index(const InstDesc& d, int a, bool odd, int x, int y,
+                                               int z) {
+  if (!odd) return a * d.pop_stride + cell_off(x, y, z, d.ny, d.nxp);
+  int xs = x - cx(a), ys = y - cy(a), zs = z - cz(a);
+  xs = xs < 0 ? xs + d.nx : (xs >= d.nx ? xs - d.nx : xs);
+  ys = ys < 0 ? ys + d.ny : (ys >= d.ny ? ys - d.ny : ys);
+  zs = zs < 0 ? zs + d.nz : (zs >= d.nz ? zs - d.nz : zs);
+  return opp(a) * d.pop_stride + cell_off(xs, ys, zs, d.ny, d.nxp);
+}
+
+template <typename T>
+__global__ void k_init(InstDesc d, bool odd, int mode, double amp, const double* __restrict__ u,
+                       int64_t ustride, int64_t c0, int64_t n) {
+  T* fb = static_cast<T*>(d.f);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int x, y, z;
+    cell_xyz(c0 + k, d.nx, d.ny, x, y, z);
+    double ux = 0.0, uy = 0.0, uz = 0.0, drho = 0.0;
+    if (mode == 1 || mode == 2) {
+      double sX, cX, sY, cY, sZ, cZ;
+      sincospi(2.0 * x / d.nx, &sX, &cX);
+      sincospi(2.0 * y / d.ny, &sY, &cY);
+      sincospi(2.0 * z / d.nz, &sZ, &cZ);
+      if (mode == 1) {
+        ux = amp * sX * cY * cZ;
+        uy = -amp * cX * sY * cZ;
+      } else {
+        ux = amp * sX * cY;
+        uy = -amp * cX * sY;
+        // pressure of the 2-D vortex: p = (A^2/4)(cos 2X + cos 2Y), drho = 3 p
+        drho = 0.75 * amp * amp * ((cX * cX - sX * sX) + (cY * cY - sY * sY));
+      }
+    } else if (mode == 3) {
+      ux = u[k];
+      uy = u[ustride + k];
+      uz = u[2 * ustride + k];
+    }
+    double f[19];
+    equilibrium_fp64(drho, ux, uy, uz, f);
+#pragma unroll
+    for (int a = 0; a < 19; ++a) fb[canon_index(d, a, odd, x, y, z)] = Storage<T>::pack((float)f[a]);
+  }
+}
+
+template <typename T>
+__global__ void k_get_pop(InstDesc d, bool odd, int a, double* __restrict__ out, int shifted,
+                          int64_t c0, int64_t n) {
+  const T* fb = static_cast<const T*>(d.f);
+  const double w = shifted ? 0.0 : weight(a);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int x, y, z;
+    cell_xyz(c0 + k, d.nx, d.ny, x, y, z);
+    out[k] = (double)Storage<T>::cvt(fb[canon_index(d, a, odd, x, y, z)]) + w;
+  }
+}
+
+template <typename T>
+__global__ void k_set_pop(InstDesc d, bool odd, int a, const double* __restrict__ in, int shifted,
+                          int64_t c0, int64_t n) {
+  T* fb = static_cast<T*>(d.f);
+  const double w = shifted ? 0.0 : weight(a);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int x, y, z;
+    cell_xyz(c0 + k, d.nx, d.ny, x, y, z);
+    fb[canon_index(d, a, odd, x, y, z)] = Storage<T>::pack((float)(in[k] - w));
+  }
+}
+
+// sa, sb: copies of slots a and opp(a) taken at the old parity.
+template <typename T>
+__global__ void k_relayout(InstDesc d, bool from_odd, int a, const T* __restrict__ sa,
+                           const T* __restrict__ sb) {
+  T* fb = static_cast<T*>(d.f);
+  const int b = opp(a);
+  const int64_t n = (int64_t)d.nx * d.ny * d.nz;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int x, y, z;
+    cell_xyz(k, d.nx, d.ny, x, y, z);
+    const int64_t o = cell_off(x, y, z, d.ny, d.nxp);
+    // canonical values at this cell, from the old layout
+    double fa, fbv;
+    if (!from_odd) {
+      fa = Storage<T>::cvt(sa[o]);
+      fbv = Storage<T>::cvt(sb[o]);
+    } else {
+      // f_a(x) = slot b of x - c_a ; f_b(x) = slot a of x + c_a
+      int xs = x - cx(a), ys = y - cy(a), zs = z - cz(a);
+      xs = (xs + d.nx) % d.nx;
+      ys = (ys + d.ny) % d.ny;
+      zs = (zs + d.nz) % d.nz;
+      int xq = x + cx(a), yq = y + cy(a), zq = z + cz(a);
+      xq = (xq + d.nx) % d.nx;
+      yq = (yq + d.ny) % d.ny;
+      zq = (zq + d.nz) % d.nz;
+      fa = Storage<T>::cvt(sb[cell_off(xs, ys, zs, d.ny, d.nxp)]);
+      fbv = Storage<T>::cvt(sa[cell_off(xq, yq, zq, d.ny, d.nxp)]);
+    }
+    const bool to_odd = !from_odd;
+    fb[canon_index(d, a, to_odd, x, y, z)] = Storage<T>::pack((float)fa);
+    fb[canon_index(d, b, to_odd, x, y, z)] = Storage<T>::pack((float)fbv);
+  }
+}
+
+__global__ void k_finish(const double* __restrict__ partials, int ninst, int grid,
+                         double* __restrict__ results, double* ring, unsigned long long* seq,
+                         int cap, uint32_t* err) {
+  const unsigned long long slot = ring ? (*seq % (unsigned long long)cap) : 0ull;
+  for (int idx = threadIdx.x; idx < ninst * kNP; idx += blockDim.x) {
+    const int i = idx / kNP, k = idx - i * kNP;
+    double r = (k == P_THMIN) ? DBL_MAX : (k == P_THMAX ? -DBL_MAX : 0.0);
+    for (int b = 0; b < grid; ++b) {
+      const double* p = partials + ((int64_t)i * grid + b) * kNP;
+      if (p[P_CELLS] == 0.0) continue;  // block saw no cell of instance i
+      const double v = p[k];
+      if (k == P_THMIN) r = fmin(r, v);
+      else if (k == P_THMAX) r = fmax(r, v);
+      else r += v;
+    }
+    results[idx] = r;
+    if (k == P_BAD && r > 0.0) atomicOr(err, ERR_NONFINITE);
+    if (ring) ring[slot * (unsigned long long)(ninst * kNP) + idx] = r;
+  }
+  __syncthreads();
+  if (ring && threadIdx.x == 0) *seq += 1ull;
+}
+
+// Exact integer shell: s with s^2 - s + 1 <= K <= s^2 + s (s - 1/2 <= sqrt K < s + 1/2).
+__device__ __forceinline__ int shell_of(long long K) {
+  long long r = (long long)sqrt((double)K);
+  while (r * r > K) --r;
+  while ((r + 1) * (r + 1) <= K) ++r;
+  return (int)(K > r * r + r ? r + 1 : r);
+}
+
+__global__ void k_spec_bin(const float2* __restrict__ c, int nx, int ny, int nz, int kmax,
+                           double* __restrict__ partials) {
+  extern __shared__ double sh[];
+  for (int s = threadIdx.x; s <= kmax; s += blockDim.x) sh[s] = 0.0;
+  __syncthreads();
+  const int nxh = nx / 2 + 1;
+  const int64_t n = (int64_t)nz * ny * nxh;
+  const double ncell = (double)nx * ny * nz;
+  const double scale = 0.5 / (ncell * ncell);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % nxh);
+    const int64_t rest = i / nxh;
+    const int ky = (int)(rest % ny);
+    const int kz = (int)(rest / ny);
+    const long long sy = ky <= ny / 2 ? ky : ky - ny;
+    const long long sz = kz <= nz / 2 ? kz : kz - nz;
+    const long long K = (long long)kx * kx + sy * sy + sz * sz;
+    const int s = shell_of(K);
+    if (s > kmax) continue;
+    // the R2C half-spectrum holds each kx > 0 mode once for the pair (k, -k),
+    // except kx = 0 and the Nyquist plane kx = nx/2 (even nx)
+    const double wgt = (kx == 0 || (2 * kx == nx)) ? 1.0 : 2.0;
+    const float2 v = c[i];
+    atomicAdd(&sh[s], wgt * scale * ((double)v.x * v.x + (double)v.y * v.y));
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s <= kmax; s += blockDim.x)
+    partials[(int64_t)blockIdx.x * (kmax + 1) + s] += sh[s];
+}
+
+__global__ void k_sum_cols(const double* __restrict__ p, int rows, int cols, double* __restrict__ out) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x) {
+    double r = 0.0;
+    for (int b = 0; b < rows; ++b) r += p[(int64_t)b * cols + c];
+    out[c] = r;
+  }
+}
+
+__global__ void k_struct(const float* __restrict__ u, int nx, int ny, int nz, int r,
+                         double* __restrict__ partials) {
+  const int64_t n = (int64_t)nx * ny * nz;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  const int rx = r % nx, ry = r % ny, rz = r % nz;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int x, y, z;
+    cell_xyz(i, nx, ny, x, y, z);
+    const int xr = x + rx >= nx ? x + rx - nx : x + rx;
+    const int yr = y + ry >= ny ? y + ry - ny : y + ry;
+    const int zr = z + rz >= nz ? z + rz - nz : z + rz;
+    const double d3[3] = {
+        (double)u[((int64_t)z * ny + y) * nx + xr] - (double)u[i],
+        (double)u[n + ((int64_t)z * ny + yr) * nx + x] - (double)u[n + i],
+        (double)u[2 * n + ((int64_t)zr * ny + y) * nx + x] - (double)u[2 * n + i]};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double p = d3[a];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        acc[k] += p;
+        p *= d3[a];
+      }
+    }
+  }
+  __shared__ double red[32][6];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    double v = acc[k];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) red[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][threadIdx.x];
+    partials[(int64_t)blockIdx.x * 6 + threadIdx.x] = v;
+  }
+}
+
+int grid_for(int64_t n) {
+  int64_t b = (n + kAuxThreads - 1) / kAuxThreads;
+  if (b < 1) b = 1;
+  if (b > 4096) b = 4096;
+  return (int)b;
+}
+
+template <typename T>
+cudaError_t init_t(const InstDesc& d, bool odd, int mode, double amp, const double* u,
+                   int64_t ustride, int64_t c0, int64_t n, cudaStream_t st) {
+  k_init<T><<<grid_for(n), kAuxThreads, 0, st>>>(d, odd, mode, amp, u, ustride, c0, n);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_init(const InstDesc& d, int precision, bool odd, int mode, double amp,
+                        const double* u, int64_t ustride, int64_t c0, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  switch (precision) {
+    case 0: return init_t<float>(d, odd, mode, amp, u, ustride, c0, n, st);
+    case 1: return init_t<__half>(d, odd, mode, amp, u, ustride, c0, n, st);
+    case 2: return init_t<__nv_bfloat16>(d, odd, mode, amp, u, ustride, c0, n, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_get_pop(const InstDesc& d, int precision, bool odd, int a, double* out,
+                           int shifted, int64_t c0, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int g = grid_for(n);
+  switch (precision) {
+    case 0: k_get_pop<float><<<g, kAuxThreads, 0, st>>>(d, odd, a, out, shifted, c0, n); break;
+    case 1: k_get_pop<__half><<<g, kAuxThreads, 0, st>>>(d, odd, a, out, shifted, c0, n); break;
+    case 2: k_get_pop<__nv_bfloat16><<<g, kAuxThreads, 0, st>>>(d, odd, a, out, shifted, c0, n); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_pop(const InstDesc& d, int precision, bool odd, int a, const double* in,
+                           int shifted, int64_t c0, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int g = grid_for(n);
+  switch (precision) {
+    case 0: k_set_pop<float><<<g, kAuxThreads, 0, st>>>(d, odd, a, in, shifted, c0, n); break;
+    case 1: k_set_pop<__half><<<g, kAuxThreads, 0, st>>>(d, odd, a, in, shifted, c0, n); break;
+    case 2: k_set_pop<__nv_bfloat16><<<g, kAuxThreads, 0, st>>>(d, odd, a, in, shifted, c0, n); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_relayout_pair(const InstDesc& d, int precision, bool from_odd, int a,
+                                 void* scratch, cudaStream_t st) {
+  const size_t es = precision == 0 ? 4 : 2;
+  const size_t plane = (size_t)d.pop_stride * es;
+  char* s = static_cast<char*>(scratch);
+  const char* base = static_cast<const char*>(d.f);
+  cudaError_t e = cudaMemcpyAsync(s, base + (size_t)a * plane, plane, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(s + plane, base + (size_t)opp(a) * plane, plane, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return e;
+  const int g = grid_for((int64_t)d.nx * d.ny * d.nz);
+  switch (precision) {
+    case 0: k_relayout<float><<<g, kAuxThreads, 0, st>>>(d, from_odd, a, (const float*)s, (const float*)(s + plane)); break;
+    case 1: k_relayout<__half><<<g, kAuxThreads, 0, st>>>(d, from_odd, a, (const __half*)s, (const __half*)(s + plane)); break;
+    case 2: k_relayout<__nv_bfloat16><<<g, kAuxThreads, 0, st>>>(d, from_odd, a, (const __nv_bfloat16*)s, (const __nv_bfloat16*)(s + plane)); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish(const double* partials, int ninst, int grid, double* results,
+                          double* ring, unsigned long long* seq, int cap, uint32_t* err,
+                          cudaStream_t st) {
+  k_finish<<<1, 256, 0, st>>>(partials, ninst, grid, results, ring, seq, cap, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spec_bin(const void* coeffs, int nx, int ny, int nz, int kmax,
+                            double* partials, int blocks, cudaStream_t st) {
+  k_spec_bin<<<blocks, kAuxThreads, (size_t)(kmax + 1) * sizeof(double), st>>>(
+      static_cast<const float2*>(coeffs), nx, ny, nz, kmax, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spec_finish(const double* partials, int blocks, int kmax, double* E,
+                               cudaStream_t st) {
+  return launch_sum_cols(partials, blocks, kmax + 1, E, st);
+}
+
+cudaError_t launch_sum_cols(const double* partials, int rows, int cols, double* out,
+                            cudaStream_t st) {
+  k_sum_cols<<<(cols + 255) / 256, 256, 0, st>>>(partials, rows, cols, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_struct(const float* u, int nx, int ny, int nz, int r, double* partials,
+                          int blocks, cudaStream_t st) {
+  k_struct<<<blocks, kAuxThreads, 0, st>>>(u, nx, ny, nz, r, partials);
+  return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,282 @@
+// Device building blocks of the D3Q19 Guo-MRT-Smagorinsky step: velocity
+// set, storage conversions, and the per-cell collision in FP32 registers.
+//
+// The collision follows Eq. (mrt_les_guo) (Sec. 2.3) with the moment basis,
+// relaxation rates and equilibrium / force moments of App. B, the strain of
+// Eq. (yu_strain) and the closure of Eqs. (eddy_visc), (les_viscosity),
+// (strain_norm).  The 19x19 transforms are not multiplied out: the basis is
+// orthogonal with integer rows, so
+//   forward  m = M f'   uses the sums s_p and differences d_p of the nine
+//                        opposite pairs (even rows see only s_p, odd rows d_p);
+//   inverse  f* = M^T diag(1/|M_k|^2) m*  splits into an even part E_p and an
+//                        odd part O_p per pair, f*_{+c} = E_p + O_p,
+//                        f*_{-c} = E_p - O_p.
+// About 300 FP32 operations per cell, all in registers.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cstdint>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// D3Q19 velocities in the paper's order (App. B table, index 1..19 -> 0..18);
+// a and a^1 are opposite for a < 18, 18 is the rest particle.
+__host__ __device__ constexpr int cx(int a) {
+  constexpr int t[19] = {1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 0};
+  return t[a];
+}
+__host__ __device__ constexpr int cy(int a) {
+  constexpr int t[19] = {0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 1, -1, 1, -1, 0, 0, 0, 0, 0};
+  return t[a];
+}
+__host__ __device__ constexpr int cz(int a) {
+  constexpr int t[19] = {0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1, 0};
+  return t[a];
+}
+__host__ __device__ constexpr int opp(int a) { return a == 18 ? 18 : (a ^ 1); }
+__host__ __device__ constexpr double weight(int a) {
+  return a == 18 ? 1.0 / 3.0 : (a < 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+// Storage <-> FP32 conversions.
+template <typename T> struct Storage;
+template <> struct Storage<float> {
+  static __device__ __forceinline__ float load(const float* p) { return *p; }
+  static __device__ __forceinline__ float cvt(float v) { return v; }
+  static __device__ __forceinline__ float pack(float v) { return v; }
+};
+template <> struct Storage<__half> {
+  static __device__ __forceinline__ float load(const __half* p) { return __half2float(*p); }
+  static __device__ __forceinline__ float cvt(__half v) { return __half2float(v); }
+  static __device__ __forceinline__ __half pack(float v) { return __float2half_rn(v); }
+};
+template <> struct Storage<__nv_bfloat16> {
+  static __device__ __forceinline__ float load(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+  static __device__ __forceinline__ float cvt(__nv_bfloat16 v) { return __bfloat162float(v); }
+  static __device__ __forceinline__ __nv_bfloat16 pack(float v) { return __float2bfloat16_rn(v); }
+};
+
+// Per-cell quantities of the collision, used by the fused statistics.
+struct CellDiag {
+  float drho, ux, uy, uz, snorm, theta;
+};
+
+// Squared norms |M_k|^2 of the rows of M (orthogonal basis, App. B).
+#define LBM_N0 19.f
+#define LBM_N1 2394.f
+#define LBM_N2 252.f
+#define LBM_N3 10.f
+#define LBM_N4 40.f
+#define LBM_N9 36.f
+#define LBM_N10 72.f
+#define LBM_N11 12.f
+#define LBM_N12 24.f
+#define LBM_N13 4.f
+#define LBM_N16 8.f
+
+// Fixed relaxation rates of Eq. (relaxation-matrix): s1 (energy), s2 (energy
+// square), s4 (heat flux), s10 = s12, s16 = s17 = s18; conserved moments have
+// rate 1 and the five shear moments the local s_nu.
+#define LBM_S1 1.19f
+#define LBM_S2 1.4f
+#define LBM_S4 1.2f
+#define LBM_S10 1.4f
+#define LBM_S16 1.98f
+
+// In place: f (19 weight-shifted pre-collision populations) -> f* (post-collision),
+// force F at the cell.  nu0, s_nu0: bare viscosity and shear rate; C: Smagorinsky
+// constant (Delta = dx = 1).
+__device__ __forceinline__ void mrt_collide(float (&f)[19], const float Fx, const float Fy,
+                                            const float Fz, const float nu0, const float s_nu0,
+                                            const float C, CellDiag& dg) {
+  // ---- m = M f' via pair sums and differences -------------------------------
+  float s[9], d[9];
+#pragma unroll
+  for (int p = 0; p < 9; ++p) {
+    s[p] = f[2 * p] + f[2 * p + 1];
+    d[p] = f[2 * p] - f[2 * p + 1];
+  }
+  const float f18 = f[18];
+  const float A = s[0] + s[1] + s[2];           // axis links
+  const float Dxy = s[3] + s[4], Dyz = s[5] + s[6], Dxz = s[7] + s[8];
+  const float D = Dxy + Dyz + Dxz;              // diagonal links
+  const float m0 = A + D + f18;                 // drho
+  const float m1 = -11.f * A + 8.f * D - 30.f * f18;
+  const float m2 = -4.f * A + D + 12.f * f18;
+  const float jx = d[0] + d[3] + d[4] + d[7] + d[8];
+  const float jy = d[1] + d[3] - d[4] + d[5] + d[6];
+  const float jz = d[2] + d[5] - d[6] + d[7] - d[8];
+  const float m4 = jx - 5.f * d[0];
+  const float m6 = jy - 5.f * d[1];
+  const float m8 = jz - 5.f * d[2];
+  const float Pxx = 2.f * s[0] - s[1] - s[2];
+  const float Qxx = Dxy - 2.f * Dyz + Dxz;
+  const float m9 = Pxx + Qxx;
+  const float m10 = -2.f * Pxx + Qxx;
+  const float Pww = s[1] - s[2];
+  const float Qww = Dxy - Dxz;
+  const float m11 = Pww + Qww;
+  const float m12 = -2.f * Pww + Qww;
+  const float m13 = s[3] - s[4];
+  const float m14 = s[5] - s[6];
+  const float m15 = s[7] - s[8];
+  const float m16 = d[3] + d[4] - d[7] - d[8];
+  const float m17 = -d[3] + d[4] + d[5] + d[6];
+  const float m18 = -d[5] + d[6] + d[7] - d[8];
+
+  // ---- macroscopic fields, Eqs. (macroscopic_eq), (guo_velocity) ------------
+  const float rho = 1.f + m0;
+  const float irho = 1.f / rho;
+  const float gx = jx + 0.5f * Fx, gy = jy + 0.5f * Fy, gz = jz + 0.5f * Fz;  // rho u
+  const float ux = gx * irho, uy = gy * irho, uz = gz * irho;
+  const float uxx = ux * ux, uyy = uy * uy, uzz = uz * uz;
+  const float uu = uxx + uyy + uzz;
+
+  // ---- equilibrium moments (Eq. meq_fm) and non-equilibrium parts ----------
+  const float eq1 = -11.f * m0 + 19.f * rho * uu;
+  const float eq2 = (-475.f / 63.f) * rho * uu;
+  const float n1 = m1 - eq1;
+  const float n9 = m9 - rho * (2.f * uxx - uyy - uzz);
+  const float n11 = m11 - rho * (uyy - uzz);
+  const float n13 = m13 - gx * uy;
+  const float n14 = m14 - gy * uz;
+  const float n15 = m15 - gx * uz;
+
+  // ---- strain (Eq. yu_strain, s1 = 1.19, s9 = s_nu0) and closure -----------
+  const float a1 = (LBM_S1 / 38.f) * n1;
+  const float Sxx = -a1 - 0.5f * s_nu0 * n9;
+  const float Syy = -a1 + 0.25f * s_nu0 * (n9 - 3.f * n11);
+  const float Szz = -a1 + 0.25f * s_nu0 * (n9 + 3.f * n11);
+  const float Sxy = -1.5f * s_nu0 * n13;
+  const float Sxz = -1.5f * s_nu0 * n15;
+  const float Syz = -1.5f * s_nu0 * n14;
+  const float SS = Sxx * Sxx + Syy * Syy + Szz * Szz + 2.f * (Sxy * Sxy + Sxz * Sxz + Syz * Syz);
+  const float snorm = sqrtf(2.f * SS);          // Eq. (strain_norm)
+  const float theta = 3.f * (nu0 + C * snorm);  // tau_e - 1/2, Eq. (les_viscosity)
+  const float snu = 1.f / (0.5f + theta);
+  const float h = 1.f - 0.5f * snu;
+
+  // ---- force moments F_m (Eq. meq_fm) --------------------------------------
+  const float uFx = ux * Fx, uFy = uy * Fy, uFz = uz * Fz;
+  const float uF = uFx + uFy + uFz;
+  const float tF = 2.f * uFx - uFy - uFz;
+  const float wF = uFy - uFz;
+
+  // ---- m* = m - Lambda (m - m^eq) + (I - Lambda/2) F_m, scaled by 1/|M_k|^2
+  const float mu0 = m0 * (1.f / LBM_N0);
+  const float mu1 = (m1 - LBM_S1 * n1 + (1.f - 0.5f * LBM_S1) * 38.f * uF) * (1.f / LBM_N1);
+  const float mu2 = (m2 - LBM_S2 * (m2 - eq2) + (1.f - 0.5f * LBM_S2) * (-11.f) * uF) * (1.f / LBM_N2);
+  const float mu3 = (jx + Fx) * (1.f / LBM_N3);
+  const float mu5 = (jy + Fy) * (1.f / LBM_N3);
+  const float mu7 = (jz + Fz) * (1.f / LBM_N3);
+  // heat-flux moments: m^eq = -2/3 rho u, F_m = -2/3 F
+  const float mu4 = (m4 - LBM_S4 * (m4 + (2.f / 3.f) * gx) - (1.f - 0.5f * LBM_S4) * (2.f / 3.f) * Fx) * (1.f / LBM_N4);
+  const float mu6 = (m6 - LBM_S4 * (m6 + (2.f / 3.f) * gy) - (1.f - 0.5f * LBM_S4) * (2.f / 3.f) * Fy) * (1.f / LBM_N4);
+  const float mu8 = (m8 - LBM_S4 * (m8 + (2.f / 3.f) * gz) - (1.f - 0.5f * LBM_S4) * (2.f / 3.f) * Fz) * (1.f / LBM_N4);
+  const float mu9 = (m9 - snu * n9 + h * 2.f * tF) * (1.f / LBM_N9);
+  const float mu10 = ((1.f - LBM_S10) * m10 - (1.f - 0.5f * LBM_S10) * tF) * (1.f / LBM_N10);
+  const float mu11 = (m11 - snu * n11 + h * 2.f * wF) * (1.f / LBM_N11);
+  const float mu12 = ((1.f - LBM_S10) * m12 - (1.f - 0.5f * LBM_S10) * wF) * (1.f / LBM_N12);
+  const float mu13 = (m13 - snu * n13 + h * (ux * Fy + uy * Fx)) * (1.f / LBM_N13);
+  const float mu14 = (m14 - snu * n14 + h * (uy * Fz + uz * Fy)) * (1.f / LBM_N13);
+  const float mu15 = (m15 - snu * n15 + h * (ux * Fz + uz * Fx)) * (1.f / LBM_N13);
+  const float mu16 = (1.f - LBM_S16) * m16 * (1.f / LBM_N16);
+  const float mu17 = (1.f - LBM_S16) * m17 * (1.f / LBM_N16);
+  const float mu18 = (1.f - LBM_S16) * m18 * (1.f / LBM_N16);
+
+  // ---- f* = M^T mu: even part per pair, odd part per pair ------------------
+  const float ca = mu0 - 11.f * mu1 - 4.f * mu2;   // axis columns: rows 0, 1, 2
+  const float cd = mu0 + 8.f * mu1 + mu2;          // diagonal columns
+  const float e9 = mu9 + mu10, e11 = mu11 + mu12;
+  const float E0 = ca + 2.f * mu9 - 4.f * mu10;
+  const float E1 = ca - mu9 + 2.f * mu10 + mu11 - 2.f * mu12;
+  const float E2 = ca - mu9 + 2.f * mu10 - mu11 + 2.f * mu12;
+  const float Exy = cd + e9 + e11;
+  const float Eyz = cd - 2.f * e9;
+  const float Exz = cd + e9 - e11;
+  const float X = mu3 + mu4, Y = mu5 + mu6, Z = mu7 + mu8;
+  const float O0 = mu3 - 4.f * mu4;
+  const float O1 = mu5 - 4.f * mu6;
+  const float O2 = mu7 - 4.f * mu8;
+  const float O3 = X + Y + (mu16 - mu17);
+  const float O4 = X - Y + (mu16 + mu17);
+  const float O5 = Y + Z + (mu17 - mu18);
+  const float O6 = Y - Z + (mu17 + mu18);
+  const float O7 = X + Z + (mu18 - mu16);
+  const float O8 = X - Z - (mu16 + mu18);
+  f[0] = E0 + O0;                f[1] = E0 - O0;
+  f[2] = E1 + O1;                f[3] = E1 - O1;
+  f[4] = E2 + O2;                f[5] = E2 - O2;
+  f[6] = Exy + mu13 + O3;        f[7] = Exy + mu13 - O3;
+  f[8] = Exy - mu13 + O4;        f[9] = Exy - mu13 - O4;
+  f[10] = Eyz + mu14 + O5;       f[11] = Eyz + mu14 - O5;
+  f[12] = Eyz - mu14 + O6;       f[13] = Eyz - mu14 - O6;
+  f[14] = Exz + mu15 + O7;       f[15] = Exz + mu15 - O7;
+  f[16] = Exz - mu15 + O8;       f[17] = Exz - mu15 - O8;
+  f[18] = mu0 - 30.f * mu1 + 12.f * mu2;
+
+  dg.drho = m0;
+  dg.ux = ux;
+  dg.uy = uy;
+  dg.uz = uz;
+  dg.snorm = snorm;
+  dg.theta = theta;
+}
+
+// Local equilibrium f' = M^-1 m^eq(drho, u) (App. B) in FP64, for
+// initialisation: m^eq has entries in rows 0-9, 11, 13-15 only.
+__device__ __forceinline__ void equilibrium_fp64(double drho, double ux, double uy, double uz,
+                                                 double (&f)[19]) {
+  const double rho = 1.0 + drho;
+  const double uxx = ux * ux, uyy = uy * uy, uzz = uz * uz, uu = uxx + uyy + uzz;
+  const double mu0 = drho / 19.0;
+  const double mu1 = (-11.0 * drho + 19.0 * rho * uu) / 2394.0;
+  const double mu2 = (-475.0 / 63.0) * rho * uu / 252.0;
+  const double mu3 = rho * ux / 10.0, mu5 = rho * uy / 10.0, mu7 = rho * uz / 10.0;
+  const double mu4 = -2.0 * rho * ux / 3.0 / 40.0;
+  const double mu6 = -2.0 * rho * uy / 3.0 / 40.0;
+  const double mu8 = -2.0 * rho * uz / 3.0 / 40.0;
+  const double mu9 = rho * (2.0 * uxx - uyy - uzz) / 36.0;
+  const double mu11 = rho * (uyy - uzz) / 12.0;
+  const double mu13 = rho * ux * uy / 4.0, mu14 = rho * uy * uz / 4.0, mu15 = rho * ux * uz / 4.0;
+  const double ca = mu0 - 11.0 * mu1 - 4.0 * mu2;
+  const double cd = mu0 + 8.0 * mu1 + mu2;
+  const double E0 = ca + 2.0 * mu9;
+  const double E1 = ca - mu9 + mu11;
+  const double E2 = ca - mu9 - mu11;
+  const double Exy = cd + mu9 + mu11, Eyz = cd - 2.0 * mu9, Exz = cd + mu9 - mu11;
+  const double X = mu3 + mu4, Y = mu5 + mu6, Z = mu7 + mu8;
+  const double O0 = mu3 - 4.0 * mu4, O1 = mu5 - 4.0 * mu6, O2 = mu7 - 4.0 * mu8;
+  const double O3 = X + Y, O4 = X - Y, O5 = Y + Z, O6 = Y - Z, O7 = X + Z, O8 = X - Z;
+  f[0] = E0 + O0;          f[1] = E0 - O0;
+  f[2] = E1 + O1;          f[3] = E1 - O1;
+  f[4] = E2 + O2;          f[5] = E2 - O2;
+  f[6] = Exy + mu13 + O3;  f[7] = Exy + mu13 - O3;
+  f[8] = Exy - mu13 + O4;  f[9] = Exy - mu13 - O4;
+  f[10] = Eyz + mu14 + O5; f[11] = Eyz + mu14 - O5;
+  f[12] = Eyz - mu14 + O6; f[13] = Eyz - mu14 - O6;
+  f[14] = Exz + mu15 + O7; f[15] = Exz + mu15 - O7;
+  f[16] = Exz - mu15 + O8; f[17] = Exz - mu15 - O8;
+  f[18] = mu0 - 30.0 * mu1 + 12.0 * mu2;
+}
+
+__device__ __forceinline__ int wrap_dec(int i, int n) { return i == 0 ? n - 1 : i - 1; }
+__device__ __forceinline__ int wrap_inc(int i, int n) { return i == n - 1 ? 0 : i + 1; }
+
+// Position of cell (x, y, z) in one population plane of an instance.
+__device__ __forceinline__ int64_t cell_off(int x, int y, int z, int ny, int nxp) {
+  return ((int64_t)z * ny + y) * nxp + x;
+}
+
+// Index of the instance owning global tile t (tiles are sorted by instance).
+__device__ __forceinline__ int find_instance(const InstDesc* __restrict__ insts, int ninst,
+                                             int64_t t) {
+  int i = 0;
+  while (i + 1 < ninst && t >= insts[i].tile_end) ++i;
+  return i;
+}
+
+}  // namespace lbm

@@ -1,0 +1,71 @@
+// Host-side launchers of the device kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+struct LaunchArgs {
+  const InstDesc* insts;   // device table
+  int ninst;
+  int64_t tile_lo, tile_hi;
+  int precision;           // 0 fp32, 1 fp16, 2 bf16
+  bool odd;                // AA parity of the step (time t odd)
+  int mode;                // MODE_STEP | MODE_STEP_STATS | MODE_DIAG
+  StatsArgs sa;
+  DiagOut dout;
+  int grid, threads;
+  // TMA kernel configuration
+  int stages;
+  int smem_bytes;          // dynamic shared memory of the TMA kernel
+  int tile_bytes_max;      // bytes of one stage (19 segments)
+  uint32_t* err;           // device error word
+  long long spin_limit;    // bounded waits: polls before giving up
+};
+
+cudaError_t launch_step_direct(const LaunchArgs& la, cudaStream_t st);
+int direct_max_blocks_per_sm(int precision, int threads);
+
+cudaError_t launch_step_tma(const LaunchArgs& la, cudaStream_t st);
+int tma_max_blocks_per_sm(int precision, int threads, int smem_bytes);
+cudaError_t tma_prepare(int precision, int smem_bytes);
+
+// Initial condition: f' = equilibrium of (drho, u), written at AA parity `odd`,
+// for the canonical cells [c0, c0 + n) (linear index (z ny + y) nx + x).
+// mode: 0 rest, 1 TGV3D, 2 TGV2D, 3 velocity from device FP64 `u` with
+// components at u[k], u[ustride + k], u[2 ustride + k] for cell c0 + k.
+cudaError_t launch_init(const InstDesc& d, int precision, bool odd, int mode, double amp,
+                        const double* u, int64_t ustride, int64_t c0, int64_t n,
+                        cudaStream_t st);
+// Canonical population a of cells [c0, c0 + n) -> FP64 out[0..n) (+ w_a when !shifted).
+cudaError_t launch_get_pop(const InstDesc& d, int precision, bool odd, int a, double* out,
+                           int shifted, int64_t c0, int64_t n, cudaStream_t st);
+cudaError_t launch_set_pop(const InstDesc& d, int precision, bool odd, int a, const double* in,
+                           int shifted, int64_t c0, int64_t n, cudaStream_t st);
+// Re-lay out the pair (a, opp a) from parity `from_odd` to the other parity
+// using a scratch buffer of 2 * nz * ny * nxp storage elements.
+cudaError_t launch_relayout_pair(const InstDesc& d, int precision, bool from_odd, int a,
+                                 void* scratch, cudaStream_t st);
+// Reduce block partials: results[i][kNP] for instances i in [0, ninst); when
+// ring != null also append to ring[(seq % cap)][ninst][kNP] and bump *seq.
+cudaError_t launch_finish(const double* partials, int ninst, int grid, double* results,
+                          double* ring, unsigned long long* seq, int cap, uint32_t* err,
+                          cudaStream_t st);
+// Shell sums of |u_hat|^2 / ncell^2 from an R2C spectrum [nz][ny][nx/2+1]:
+// partials [blocks][kmax + 1] (accumulated onto), then summed by launch_spec_finish.
+cudaError_t launch_spec_bin(const void* coeffs, int nx, int ny, int nz, int kmax,
+                            double* partials, int blocks, cudaStream_t st);
+cudaError_t launch_spec_finish(const double* partials, int blocks, int kmax, double* E,
+                               cudaStream_t st);
+// Structure functions: partials [blocks][6] of sum over cells and axes of
+// (u_a(x + r e_a) - u_a(x))^p, p = 1..6, for velocity u [3][nz][ny][nx] FP32.
+cudaError_t launch_struct(const float* u, int nx, int ny, int nz, int r, double* partials,
+                          int blocks, cudaStream_t st);
+cudaError_t launch_sum_cols(const double* partials, int rows, int cols, double* out,
+                            cudaStream_t st);
+
+}  // namespace lbm

@@ -1,0 +1,137 @@
+// Fused FP64 statistics of the step kernels: per-thread accumulation of the
+// per-cell quantities, warp-shuffle + shared-memory block reduction into one
+// partial per block and instance (deterministic order), and the per-cell
+// outputs of the read-only diagnostic pass.
+#pragma once
+
+#include <cfloat>
+#include <cstdint>
+
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+struct Acc {
+  double s[kNSum];
+  float thmin, thmax;
+  uint32_t bad, cells;
+
+  __device__ __forceinline__ void reset() {
+#pragma unroll
+    for (int k = 0; k < kNSum; ++k) s[k] = 0.0;
+    thmin = FLT_MAX;
+    thmax = -FLT_MAX;
+    bad = 0;
+    cells = 0;
+  }
+
+  // Energy E_k = <u.u>/2, injection <F.u>, dissipation 2 nu <S_ij S_ij> with
+  // S_ij S_ij = |S|^2/2 (Eqs. energy_balance, strain_norm), theta = tau_e - 1/2.
+  __device__ __forceinline__ void add(const CellDiag& g, float Fx, float Fy, float Fz, float C) {
+    const double rho = 1.0 + (double)g.drho;
+    const double ux = g.ux, uy = g.uy, uz = g.uz;
+    const double sn = g.snorm, th = g.theta;
+    const double ss = sn * sn;
+    s[P_DRHO] += (double)g.drho;
+    s[P_MX] += rho * ux;
+    s[P_MY] += rho * uy;
+    s[P_MZ] += rho * uz;
+    s[P_UU] += ux * ux + uy * uy + uz * uz;
+    s[P_FU] += (double)Fx * ux + (double)Fy * uy + (double)Fz * uz;
+    s[P_SS] += ss;
+    s[P_NUTSS] += (double)C * sn * ss;
+    s[P_TH] += th;
+    s[P_TH2] += th * th;
+    s[P_XX] += ux * ux;
+    s[P_YY] += uy * uy;
+    s[P_ZZ] += uz * uz;
+    s[P_XY] += ux * uy;
+    s[P_XZ] += ux * uz;
+    s[P_YZ] += uy * uz;
+    thmin = fminf(thmin, g.theta);
+    thmax = fmaxf(thmax, g.theta);
+    const float chk = g.drho + g.ux + g.uy + g.uz + g.snorm;
+    bad += isfinite(chk) ? 0u : 1u;
+    cells += 1u;
+  }
+};
+
+// Reduce the accumulators of the `nthreads` threads that call this (a whole
+// block, or the consumer warps of a specialised block synchronised with named
+// barrier `bar_id`) and write kNP doubles to dst.  Fixed order: lane tree,
+// then warps in index order.
+__device__ __forceinline__ void named_sync(int bar_id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(nthreads) : "memory");
+}
+
+static __device__ __noinline__ void block_flush(Acc& acc, double* __restrict__ dst, int nthreads,
+                                         int bar_id) {
+  __shared__ double red[32][kNP];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double v[kNP];
+#pragma unroll
+  for (int k = 0; k < kNSum; ++k) v[k] = acc.s[k];
+  v[P_THMIN] = acc.thmin;
+  v[P_THMAX] = acc.thmax;
+  v[P_BAD] = acc.bad;
+  v[P_CELLS] = acc.cells;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int k = 0; k < kNP; ++k) {
+      const double o = __shfl_down_sync(0xffffffffu, v[k], off);
+      if (k == P_THMIN) v[k] = fmin(v[k], o);
+      else if (k == P_THMAX) v[k] = fmax(v[k], o);
+      else v[k] += o;
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < kNP; ++k) red[warp][k] = v[k];
+  }
+  named_sync(bar_id, nthreads);
+  if (threadIdx.x < kNP) {
+    const int k = threadIdx.x;
+    const int nw = nthreads >> 5;
+    double r = red[0][k];
+    for (int w = 1; w < nw; ++w) {
+      const double o = red[w][k];
+      if (k == P_THMIN) r = fmin(r, o);
+      else if (k == P_THMAX) r = fmax(r, o);
+      else r += o;
+    }
+    dst[k] = r;
+  }
+  named_sync(bar_id, nthreads);
+}
+
+// Per-cell outputs of the read-only diagnostic pass.
+__device__ __forceinline__ void diag_write(const DiagOut& o, const CellDiag& g, int x, int y, int z,
+                                           int nx, int ny, int nz, uint32_t* shist) {
+  const int64_t n = (int64_t)nx * ny * nz;
+  const int64_t i = ((int64_t)z * ny + y) * nx + x;
+  if (o.u) {
+    o.u[i] = g.ux;
+    o.u[n + i] = g.uy;
+    o.u[2 * n + i] = g.uz;
+  }
+  if (o.aux) {
+    o.aux[i] = g.drho;
+    o.aux[n + i] = g.snorm;
+    o.aux[2 * n + i] = g.theta;
+  }
+  if (o.plane) {
+    if (o.plane_axis == 0 && x == o.plane_index) o.plane[(int64_t)z * ny + y] = g.theta;
+    if (o.plane_axis == 1 && y == o.plane_index) o.plane[(int64_t)z * nx + x] = g.theta;
+    if (o.plane_axis == 2 && z == o.plane_index) o.plane[(int64_t)y * nx + x] = g.theta;
+  }
+  if (shist) {
+    int b = o.hist_bins;
+    const float q = g.theta * o.hist_scale;
+    if (q >= 0.f && q < (float)o.hist_bins) b = min((int)q, o.hist_bins - 1);
+    atomicAdd(&shist[b], 1u);
+  }
+}
+
+}  // namespace lbm

@@ -1,0 +1,145 @@
+// Direct-load stream + collide kernel (AA pattern, one population array).
+//
+// Even step: cell x reads f_a from its own slot a and writes f*_a to its own
+// slot opp(a).  Odd step: cell x reads f_a from slot opp(a) of x - c_a and
+// writes f*_a to slot a of x + c_a.  Each cell reads exactly the locations it
+// writes, so all cells of a step are independent (Eq. mrt_les_guo, with
+// periodic streaming of Sec. 3.1).  One thread per cell, plain coalesced
+// loads and stores; the grid walks tiles of `rows` x-lines.
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+#include "lbm_kernels.h"
+#include "lbm_reduce.cuh"
+
+namespace lbm {
+
+template <typename T, bool ODD, int MODE>
+__global__ void __launch_bounds__(256)
+k_step_direct(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64_t tile_hi,
+              StatsArgs sa, DiagOut dout) {
+  using S = Storage<T>;
+  extern __shared__ uint32_t shist[];
+  const bool use_hist = (MODE == MODE_DIAG) && dout.hist != nullptr;
+  if (use_hist) {
+    for (int i = threadIdx.x; i <= dout.hist_bins; i += blockDim.x) shist[i] = 0u;
+    __syncthreads();
+  }
+  Acc acc;
+  acc.reset();
+  int cur = -1;
+  for (int64_t t = tile_lo + blockIdx.x; t < tile_hi; t += gridDim.x) {
+    const int ii = find_instance(insts, ninst, t);
+    if (MODE != MODE_STEP && ii != cur) {
+      if (cur >= 0)
+        block_flush(acc, sa.partials + ((int64_t)cur * sa.grid + blockIdx.x) * kNP, blockDim.x, 0);
+      acc.reset();
+      cur = ii;
+    }
+    const InstDesc& d = insts[ii];
+    const int nx = d.nx, ny = d.ny, nz = d.nz, nxp = d.nxp;
+    const int64_t ps = d.pop_stride;
+    const int64_t local = t - d.tile_begin;
+    const int z = (int)(local / d.tiles_per_plane);
+    const int y0 = (int)(local - (int64_t)z * d.tiles_per_plane) * d.rows;
+    const int rows = min(d.rows, ny - y0);
+    const int ncell = rows * nx;
+    T* __restrict__ fb = static_cast<T*>(d.f);
+    const int zm = wrap_dec(z, nz), zp = wrap_inc(z, nz);
+    const float Fy = d.fy_of_z[z] + d.fconst[1];
+    const float nu0 = d.nu0, s_nu0 = d.s_nu0, C = d.C;
+    for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+      const int r = c / nx;
+      const int x = c - r * nx;
+      const int y = y0 + r;
+      const int ym = wrap_dec(y, ny), yp = wrap_inc(y, ny);
+      const int xm = wrap_dec(x, nx), xp = wrap_inc(x, nx);
+      float f[19];
+      if (!ODD) {
+        const int64_t o = cell_off(x, y, z, ny, nxp);
+#pragma unroll
+        for (int a = 0; a < 19; ++a) f[a] = S::load(fb + a * ps + o);
+      } else {
+#pragma unroll
+        for (int a = 0; a < 19; ++a) {
+          const int xs = cx(a) > 0 ? xm : (cx(a) < 0 ? xp : x);
+          const int ys = cy(a) > 0 ? ym : (cy(a) < 0 ? yp : y);
+          const int zs = cz(a) > 0 ? zm : (cz(a) < 0 ? zp : z);
+          f[a] = S::load(fb + opp(a) * ps + cell_off(xs, ys, zs, ny, nxp));
+        }
+      }
+      const float Fx = d.fx_of_y[y] + d.fconst[0];
+      const float Fz = d.fz_of_x[x] + d.fconst[2];
+      CellDiag g;
+      mrt_collide(f, Fx, Fy, Fz, nu0, s_nu0, C, g);
+      if (MODE != MODE_DIAG) {
+        if (!ODD) {
+          const int64_t o = cell_off(x, y, z, ny, nxp);
+#pragma unroll
+          for (int a = 0; a < 19; ++a) fb[opp(a) * ps + o] = S::pack(f[a]);
+        } else {
+#pragma unroll
+          for (int a = 0; a < 19; ++a) {
+            const int xd = cx(a) > 0 ? xp : (cx(a) < 0 ? xm : x);
+            const int yd = cy(a) > 0 ? yp : (cy(a) < 0 ? ym : y);
+            const int zd = cz(a) > 0 ? zp : (cz(a) < 0 ? zm : z);
+            fb[a * ps + cell_off(xd, yd, zd, ny, nxp)] = S::pack(f[a]);
+          }
+        }
+      }
+      if (MODE != MODE_STEP) acc.add(g, Fx, Fy, Fz, C);
+      if (MODE == MODE_DIAG) diag_write(dout, g, x, y, z, nx, ny, nz, use_hist ? shist : nullptr);
+    }
+  }
+  if (MODE != MODE_STEP) {
+    if (cur >= 0)
+      block_flush(acc, sa.partials + ((int64_t)cur * sa.grid + blockIdx.x) * kNP, blockDim.x, 0);
+  }
+  if (use_hist) {
+    __syncthreads();
+    for (int i = threadIdx.x; i <= dout.hist_bins; i += blockDim.x)
+      if (shist[i]) atomicAdd(&dout.hist[i], shist[i]);
+  }
+}
+
+template <typename T, bool ODD, int MODE>
+static cudaError_t launch_direct_t(const LaunchArgs& la, cudaStream_t st) {
+  const size_t smem = (MODE == MODE_DIAG && la.dout.hist) ? (size_t)(la.dout.hist_bins + 1) * 4 : 0;
+  k_step_direct<T, ODD, MODE><<<la.grid, la.threads, smem, st>>>(la.insts, la.ninst, la.tile_lo,
+                                                                   la.tile_hi, la.sa, la.dout);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t dispatch_direct(const LaunchArgs& la, cudaStream_t st) {
+  if (la.odd) {
+    if (la.mode == MODE_STEP) return launch_direct_t<T, true, MODE_STEP>(la, st);
+    if (la.mode == MODE_STEP_STATS) return launch_direct_t<T, true, MODE_STEP_STATS>(la, st);
+    return launch_direct_t<T, true, MODE_DIAG>(la, st);
+  }
+  if (la.mode == MODE_STEP) return launch_direct_t<T, false, MODE_STEP>(la, st);
+  if (la.mode == MODE_STEP_STATS) return launch_direct_t<T, false, MODE_STEP_STATS>(la, st);
+  return launch_direct_t<T, false, MODE_DIAG>(la, st);
+}
+
+cudaError_t launch_step_direct(const LaunchArgs& la, cudaStream_t st) {
+  switch (la.precision) {
+    case 0: return dispatch_direct<float>(la, st);
+    case 1: return dispatch_direct<__half>(la, st);
+    case 2: return dispatch_direct<__nv_bfloat16>(la, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int direct_max_blocks_per_sm(int precision, int threads) {
+  int n = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (precision) {
+    case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_direct<float, true, MODE_STEP>, threads, 0); break;
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_direct<__half, true, MODE_STEP>, threads, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_direct<__nv_bfloat16, true, MODE_STEP>, threads, 0); break;
+  }
+  return e == cudaSuccess ? n : 0;
+}
+
+}  // namespace lbm

@@ -1,0 +1,109 @@
+"""The C-ABI library without a GPU: it loads, exports every entry point that
+include/lbm.h declares, the ctypes structures match the C layout, and the
+host-side argument validation answers before any device call."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lbm.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2512_23116_gb300 as lbm
+    from paper_2512_23116_gb300 import _build
+    _build.build()
+    return lbm
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for core in ("lbm_create", "lbm_init_field", "lbm_step", "lbm_stats", "lbm_spectrum",
+                 "lbm_destroy"):
+        assert core in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    so = ctypes.CDLL(lib.library_path())
+    for name in _declared():
+        assert hasattr(so, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.library_path()], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if " T " in ln}
+    assert exported == set(_declared())
+    assert set(lib.EXPORTED) == set(_declared())
+
+
+def test_struct_layout_matches_c(lib):
+    prog = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "lbm.h"
+int main(void) {
+  printf("%zu %zu %zu\n", sizeof(lbm_params), sizeof(lbm_stats_t), sizeof(lbm_record_t));
+  printf("%zu %zu %zu %zu\n", offsetof(lbm_params, stream), offsetof(lbm_params, tile_rows),
+         offsetof(lbm_params, hist_max), offsetof(lbm_params, body_force));
+  printf("%zu %zu %zu\n", offsetof(lbm_stats_t, nr), offsetof(lbm_stats_t, Sp), offsetof(lbm_stats_t, F4));
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(prog)
+        subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        lines = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    sizes = [int(v) for v in lines[0].split()]
+    assert sizes == [ctypes.sizeof(lib.LbmParams), ctypes.sizeof(lib.LbmStats), ctypes.sizeof(lib.LbmRecord)]
+    offs = [int(v) for v in lines[1].split()]
+    P = lib.LbmParams
+    assert offs == [P.stream.offset, P.tile_rows.offset, P.hist_max.offset, P.body_force.offset]
+    offs = [int(v) for v in lines[2].split()]
+    S = lib.LbmStats
+    assert offs == [S.nr.offset, S.Sp.offset, S.F4.offset]
+
+
+@pytest.mark.parametrize("kw,frag", [
+    (dict(nx=0, nu0=0.01), "lattice size"),
+    (dict(nx=8, nu0=0.0, re=0.0), "nu0"),
+    (dict(nx=8, nu0=0.01, cs=-0.1), "Smagorinsky"),
+    (dict(nx=8, nu0=0.01, precision=7), "precision"),
+    (dict(nx=8, nu0=0.01, force_mode=9), "force_mode"),
+    (dict(nx=8, nu0=0.01, hist_bins=-1), "hist_bins"),
+    (dict(nx=8, nu0=0.01, kernel=5), "kernel"),
+])
+def test_invalid_parameters_rejected_before_any_device_call(lib, kw, frag):
+    nx = kw.pop("nx")
+    p = lib.make_params(nx, **kw)
+    with pytest.raises(lib.LbmError) as ei:
+        lib.lbm_create(p)
+    assert ei.value.code == lib.LBM_ERR_INVALID_ARG
+    assert frag in str(ei.value)
+
+
+def test_mixed_precision_batch_rejected(lib):
+    a = lib.make_params(8, nu0=0.01)
+    b = lib.make_params(8, nu0=0.01, precision=lib.LBM_FP16_SHIFTED)
+    with pytest.raises(lib.LbmError) as ei:
+        lib.lbm_create_batch([a, b])
+    assert ei.value.code == lib.LBM_ERR_UNSUPPORTED
+
+
+def test_no_device_is_an_error_not_a_fallback(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(lib.LbmError) as ei:
+        lib.lbm_create(lib.make_params(8, nu0=0.01))
+    assert ei.value.code == lib.LBM_ERR_CUDA

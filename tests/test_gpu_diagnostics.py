@@ -1,0 +1,197 @@
+"""GPU parity of the fused diagnostics against the oracle: domain statistics,
+theta histogram and percentiles, energy spectrum, structure functions and
+flatness, derived scales, the in-step record series, theta slices, and the
+non-finite detection (C ABI)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+from oracle import diagnostics as dg
+
+from gpu_helpers import make_pair
+
+pytestmark = pytest.mark.gpu
+
+
+def _les_case(lbm, n=24, steps=30, kind=0, stats_every=0):
+    u = synthetic.random_solenoidal(n, seed=1, urms=0.05)
+    nu0 = oracle.derive_nu0(0.043, n, 2e3)
+    F0 = oracle.forcing_amplitude(0.2, 0.043, n)
+    gpu, ref = make_pair(lbm, (n, n, n), nu0=nu0, C=0.13, force_mode=lbm.LBM_FORCE_PAPER_SIN, F0=F0,
+                         kind=kind, stats_every=stats_every, hist_bins=4096, hist_max=0.02)
+    gpu.init(lbm.LBM_INIT_VELOCITY, u=u)
+    ref.init_equilibrium(u)
+    return gpu, ref, nu0
+
+
+def test_domain_stats_match_oracle(gpu_lib):
+    lbm = gpu_lib
+    gpu, ref, nu0 = _les_case(lbm)
+    with gpu:
+        gpu.step(30)
+        st = gpu.stats(what=lbm.LBM_STATS_SPECTRUM | lbm.LBM_STATS_STRUCTURE)
+        E_gpu = gpu.spectrum(dg.max_shell(24, 24, 24))
+    ref.step(30)
+    fl = ref.fields()
+    F = ref.force_field()
+    want = dg.domain_stats(fl, F, nu0, 0.13, hist_bins=4096, hist_max=0.02)
+    assert st["step"] == 30 and st["cells"] == 24 ** 3
+    assert abs(st["mass"] - want["mass"]) < 1e-7
+    for k in ("E_k", "eps0", "eps_sgs", "theta_mean", "theta_max", "theta_min", "Kt_mean"):
+        assert math.isclose(st[k], want[k], rel_tol=2e-5), (k, st[k], want[k])
+    assert math.isclose(st["inj"], want["inj"], rel_tol=1e-4, abs_tol=1e-12)
+    for k in ("theta_var", "Kt_var"):
+        assert math.isclose(st[k], want[k], rel_tol=1e-3), (k, st[k], want[k])
+    assert np.allclose(st["uu"], want["uu"], rtol=2e-5, atol=1e-12)
+    assert np.allclose(st["momentum"], want["momentum"], atol=1e-7)
+    # percentiles: centre of the bin holding the exact percentile (width 0.02/4096)
+    width = 0.02 / 4096
+    for p, key in ((5, "theta_p05"), (50, "theta_p50"), (95, "theta_p95"), (99, "theta_p99")):
+        assert abs(st[key] - want["theta_p"][p]) <= width, (key, st[key], want["theta_p"][p])
+    # spectrum and derived scales
+    E_ref = dg.spectrum(fl["u"])
+    big = E_ref > 1e-10 * E_ref.max()
+    assert np.allclose(E_gpu[big], E_ref[big], rtol=1e-4)
+    assert np.all(np.abs(E_gpu[~big] - E_ref[~big]) <= 1e-9 * E_ref.max())
+    d = dg.derived_scales(E_ref, 24, nu0, want["E_k"])
+    for k, kk in (("L", "L"), ("eps_spec", "eps"), ("eta", "eta"), ("lambda", "lambda"),
+                  ("u_rms", "u_rms"), ("Re_lambda", "Re_lambda")):
+        assert math.isclose(st[k], d[kk], rel_tol=1e-4), (k, st[k], d[kk])
+    # structure functions and flatness
+    sf = dg.structure_functions(fl["u"])
+    assert st["r"] == sf["r"]
+    for p in (2, 4, 6):
+        assert np.allclose(st["Sp"][:, p - 1], sf["S"][:, p], rtol=1e-4)
+    assert np.allclose(st["F4"], sf["F4"], rtol=1e-4)
+    assert np.all(np.abs(st["Sp"][:, 0]) < 1e-9)  # S1 = 0 on a periodic box
+
+
+def test_histogram_counts(gpu_lib):
+    lbm = gpu_lib
+    gpu, ref, nu0 = _les_case(lbm, n=16, steps=10)
+    with gpu:
+        gpu.step(10)
+        gpu.stats()
+        h = lbm.lbm_histogram(gpu.h, 0, 4096)
+        th = gpu.fields()["theta"]
+    assert int(h.sum()) == 16 ** 3
+    idx = np.minimum((th.astype(np.float32) * np.float32(4096 / 0.02)).astype(np.int64), 4095)
+    want = np.bincount(idx.ravel(), minlength=4096)
+    assert np.array_equal(h[:4096], want)
+    assert h[4096] == 0
+
+
+def test_spectrum_single_mode(gpu_lib):
+    """u_x = A cos(2 pi (x + 2y + 2z)/N): the whole energy A^2/4 in shell 3."""
+    lbm = gpu_lib
+    n, A = 12, 0.04
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    u = np.zeros((3, n, n, n))
+    u[0] = A * np.cos(2 * np.pi * (x + 2 * y + 2 * z) / n)
+    gpu, _ = make_pair(lbm, (n, n, n), nu0=0.01, C=0.0)
+    with gpu:
+        gpu.init(lbm.LBM_INIT_VELOCITY, u=u)
+        E = gpu.spectrum(dg.max_shell(n, n, n))
+    assert math.isclose(E[3], A * A / 4, rel_tol=1e-6)
+    assert np.abs(np.delete(E, 3)).max() < 1e-12 * A * A
+
+
+def test_odd_sizes_spectrum_parseval(gpu_lib):
+    lbm = gpu_lib
+    shape = (9, 10, 11)
+    u = synthetic.random_solenoidal(11, 10, 9, seed=2)
+    gpu, _ = make_pair(lbm, shape, nu0=0.01, C=0.0)
+    with gpu:
+        gpu.init(lbm.LBM_INIT_VELOCITY, u=u)
+        kmax = dg.max_shell(11, 10, 9)
+        E = gpu.spectrum(kmax)
+        st = gpu.stats()
+    assert np.allclose(E, dg.spectrum(u, kmax), rtol=1e-4, atol=1e-12)
+    assert math.isclose(E.sum(), st["E_k"], rel_tol=1e-5)
+
+
+def test_series_records(gpu_lib):
+    lbm = gpu_lib
+    gpu, ref, nu0 = _les_case(lbm, n=16, stats_every=5)
+    with gpu:
+        gpu.step(20)
+        recs = gpu.series()
+        again = gpu.series()
+    assert [r["step"] for r in recs] == [0, 5, 10, 15]
+    assert again == []
+    F = ref.force_field()
+    for r in recs:
+        while ref.time < r["step"]:
+            ref.step(1)
+        want = dg.domain_stats(ref.fields(), F, nu0, 0.13)
+        for k in ("E_k", "eps0", "eps_sgs", "theta_mean", "theta_max", "theta_min"):
+            assert math.isclose(r[k], want[k], rel_tol=2e-5), (r["step"], k)
+        assert abs(r["mass"] - want["mass"]) < 1e-7
+
+
+def test_series_batched_instances(gpu_lib):
+    """In-step records of a two-instance handle are kept per instance."""
+    lbm = gpu_lib
+    p1 = lbm.make_params(12, nu0=0.01, cs=0.13, stats_every=4)
+    p2 = lbm.make_params(8, 6, 10, nu0=0.02, cs=0.0, stats_every=4)
+    with lbm.Lattice([p1, p2]) as g:
+        g.init(lbm.LBM_INIT_TGV3D, amplitude=0.05, inst=0)
+        g.init(lbm.LBM_INIT_TGV3D, amplitude=0.02, inst=1)
+        g.step(9)
+        r0 = g.series(inst=0)
+        r1 = g.series(inst=1)
+    assert [r["step"] for r in r0] == [0, 4, 8] == [r["step"] for r in r1]
+    assert math.isclose(r0[0]["E_k"], 0.05 ** 2 / 8, rel_tol=1e-5)
+    assert math.isclose(r1[0]["E_k"], 0.02 ** 2 / 8, rel_tol=1e-5)
+    assert math.isclose(r1[0]["theta_mean"], 3 * 0.02, rel_tol=1e-6)
+
+
+def test_theta_slice(gpu_lib):
+    lbm = gpu_lib
+    gpu, _, _ = _les_case(lbm, n=16)
+    with gpu:
+        gpu.step(6)
+        th = gpu.fields()["theta"]
+        for axis, idx in ((0, 3), (1, 0), (2, 15)):
+            s = gpu.theta_slice(axis, idx)
+            want = {0: th[:, :, idx], 1: th[:, idx, :], 2: th[idx]}[axis]
+            assert np.array_equal(s, want)
+
+
+def test_nonfinite_state_is_reported_and_recoverable(gpu_lib):
+    """Host-side fault injection: a NaN in the initial velocity surfaces as
+    LBM_ERR_UNSTABLE at the next statistics call; the handle stays usable."""
+    lbm = gpu_lib
+    n = 8
+    u = np.zeros((3, n, n, n))
+    u[0, 2, 3, 4] = np.nan
+    gpu, _ = make_pair(lbm, (n, n, n), nu0=0.01, C=0.1)
+    with gpu:
+        gpu.init(lbm.LBM_INIT_VELOCITY, u=u)
+        gpu.step(2)
+        with pytest.raises(lbm.LbmError) as ei:
+            gpu.stats()
+        assert ei.value.code == lbm.LBM_ERR_UNSTABLE
+        gpu.init(lbm.LBM_INIT_TGV3D, amplitude=0.01)
+        gpu.step(2)
+        st = gpu.stats()
+        assert st["cells"] == n ** 3 and math.isfinite(st["E_k"])
+
+
+def test_invalid_calls_on_a_live_handle(gpu_lib):
+    lbm = gpu_lib
+    gpu, _ = make_pair(lbm, (4, 4, 4), nu0=0.01, C=0.0)
+    with gpu:
+        for fn in (lambda: lbm.lbm_step(gpu.h, -1),
+                   lambda: lbm.lbm_init_field(gpu.h, 5, lbm.LBM_INIT_REST),
+                   lambda: lbm.lbm_init_field(gpu.h, 0, 42),
+                   lambda: lbm.lbm_get_theta_slice(gpu.h, 0, 3, 0, (4, 4, 4)),
+                   lambda: lbm.lbm_spectrum(gpu.h, 0, -1)):
+            with pytest.raises(lbm.LbmError) as ei:
+                fn()
+            assert ei.value.code == lbm.LBM_ERR_INVALID_ARG
+        gpu.step(1)
+        gpu.sync()

@@ -1,0 +1,213 @@
+"""GPU parity of the stream + collide step against the FP64 oracle (C ABI).
+
+FP32 storage: relative error of every full population f = f' + w at most
+1e-5 (the per-population tolerance of the 32^3 Taylor-Green case).  FP16 and
+BF16 storage: absolute error of f' at most n_steps x ulp(max |f'|) of the
+storage format (one rounding of the stored value per step)."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+from oracle import fields
+
+from gpu_helpers import KINDS, full_f_rel_error, make_pair, random_populations, ulp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("steps", [100, 37])
+def test_tgv3d_32_cubed_constant_force(gpu_lib, kind, steps):
+    """32^3 Taylor-Green, u0 = 0.05, rho = 1, nu0 = 0.01, C = 0.1, F = 1e-6 x."""
+    lbm = gpu_lib
+    n, F = 32, (1e-6, 0.0, 0.0)
+    gpu, ref = make_pair(lbm, (n, n, n), nu0=0.01, C=0.1, force_mode=lbm.LBM_FORCE_CONST, body=F,
+                         kind=kind)
+    with gpu:
+        assert gpu.config()["kind"] == kind
+        gpu.init(lbm.LBM_INIT_TGV3D, amplitude=0.05)
+        f0 = gpu.populations()
+        gpu.step(steps)
+        g = gpu.populations()
+    ref.init_equilibrium(fields.tgv3d(n, n, n, 0.05))
+    assert np.abs(f0 - ref.populations()).max() < 1e-8  # the GPU init kernel
+    ref.step(steps)
+    r = ref.populations()
+    assert full_f_rel_error(g, r) <= 1e-5
+    # mass conserved; momentum grows by ncell * F per step (Guo forcing)
+    c, _ = oracle.lattice()
+    assert abs(g.sum() - f0.sum()) < 1e-7
+    dj = c.T.astype(float) @ (g - f0).reshape(19, -1).sum(axis=1)
+    assert np.allclose(dj, np.array(F) * n ** 3 * steps, rtol=1e-3, atol=1e-6)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("shape", [(10, 12, 20), (7, 9, 33), (16, 16, 16)])
+def test_random_les_field_paper_forcing(gpu_lib, kind, shape):
+    """Random solenoidal field (seeded generator), the paper's sinusoidal forcing,
+    C = 0.13, LES viscosity; ragged sizes exercise padding and wrap."""
+    lbm = gpu_lib
+    nz, ny, nx = shape
+    u = synthetic.random_solenoidal(nx, ny, nz, seed=7, urms=0.05)
+    F0 = oracle.forcing_amplitude(0.2, 0.043, nx) * 50  # larger than the paper's, to be visible
+    gpu, ref = make_pair(lbm, shape, nu0=2.15e-4 * 10, C=0.13, force_mode=lbm.LBM_FORCE_PAPER_SIN,
+                         F0=F0, kind=kind)
+    with gpu:
+        gpu.init(lbm.LBM_INIT_VELOCITY, u=u)
+        gpu.step(51)
+        g = gpu.populations()
+        fl = gpu.fields()
+    ref.init_equilibrium(u)
+    ref.step(51)
+    assert full_f_rel_error(g, ref.populations()) <= 1e-5
+    fr = ref.fields()
+    umax = np.abs(fr["u"]).max()
+    assert np.abs(fl["u"] - fr["u"]).max() <= 1e-5 * umax
+    assert np.abs(fl["theta"] - fr["theta"]).max() <= 1e-5 * fr["theta"].max()
+    assert np.abs(fl["snorm"] - fr["snorm"]).max() <= 1e-4 * fr["snorm"].max() + 1e-9
+    assert np.abs(fl["drho"] - fr["drho"]).max() <= 1e-6
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("shape", [(1, 1, 1), (2, 1, 3), (1, 4, 5), (3, 7, 1), (2, 3, 33)])
+def test_degenerate_and_tiny_lattices(gpu_lib, kind, shape):
+    """Extents of 1 (a link wraps onto its own cell), 2 (x - 1 = x + 1) and a
+    ragged x; random near-equilibrium populations set through the ABI."""
+    lbm = gpu_lib
+    f = random_populations(shape, seed=11)
+    gpu, ref = make_pair(lbm, shape, nu0=0.05, C=0.2, force_mode=lbm.LBM_FORCE_CONST,
+                         body=(1e-5, -2e-5, 3e-5), kind=kind)
+    with gpu:
+        gpu.set_populations(f)
+        assert np.array_equal(gpu.populations(), f.astype(np.float32).astype(np.float64))
+        gpu.step(9)
+        g = gpu.populations()
+    ref.set_populations(f.astype(np.float32).astype(np.float64))
+    ref.step(9)
+    assert full_f_rel_error(g, ref.populations()) <= 1e-5
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("precision,mant", [(1, 10), (2, 7)])
+def test_shifted_low_precision_storage(gpu_lib, kind, precision, mant):
+    lbm = gpu_lib
+    n, steps = 20, 12
+    u = synthetic.random_solenoidal(n, seed=3, urms=0.05)
+    gpu, ref = make_pair(lbm, (n, n, n), nu0=0.005, C=0.13, force_mode=lbm.LBM_FORCE_PAPER_SIN,
+                         F0=1e-4, kind=kind, precision=precision)
+    ref.init_equilibrium(u)
+    fmax = np.abs(ref.populations()).max()
+    with gpu:
+        gpu.init(lbm.LBM_INIT_VELOCITY, u=u)
+        gpu.step(steps)
+        g = gpu.populations()
+    ref.step(steps)
+    err = np.abs(g - ref.populations()).max()
+    assert err <= (steps + 1) * ulp(fmax, mant), (err, ulp(fmax, mant))
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_C_zero_is_constant_viscosity(gpu_lib, kind):
+    """Sec. 2.3: C = 0 gives theta = 3 nu0 in every cell, bit for bit in FP32, and
+    matches the oracle's fixed-rate MRT path."""
+    lbm = gpu_lib
+    n, nu0 = 12, 0.0123
+    u = synthetic.random_solenoidal(n, seed=5)
+    gpu, ref = make_pair(lbm, (n, n, n), nu0=nu0, C=0.0, force_mode=lbm.LBM_FORCE_PAPER_SIN,
+                         F0=1e-4, kind=kind)
+    ref.set_fixed_rate(True)
+    with gpu:
+        gpu.init(lbm.LBM_INIT_VELOCITY, u=u)
+        gpu.step(10)
+        th = gpu.fields()["theta"]
+        g = gpu.populations()
+    assert np.all(th == float(np.float32(3.0) * np.float32(nu0)))
+    ref.init_equilibrium(u)
+    ref.step(10)
+    assert full_f_rel_error(g, ref.populations()) <= 1e-5
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_checkpoint_resume_bitwise(gpu_lib, kind):
+    """get_populations + set_time + set_populations resumes bit for bit, from an
+    odd time (twisted AA layout) into a fresh handle."""
+    lbm = gpu_lib
+    shape = (8, 10, 12)
+    u = synthetic.random_solenoidal(12, 10, 8, seed=9)
+    gpu_a, _ = make_pair(lbm, shape, nu0=0.003, C=0.13, force_mode=lbm.LBM_FORCE_PAPER_SIN, F0=1e-4, kind=kind)
+    gpu_b, _ = make_pair(lbm, shape, nu0=0.003, C=0.13, force_mode=lbm.LBM_FORCE_PAPER_SIN, F0=1e-4, kind=kind)
+    with gpu_a, gpu_b:
+        gpu_a.init(lbm.LBM_INIT_VELOCITY, u=u)
+        gpu_a.step(13)
+        snap = gpu_a.populations()
+        gpu_b.init(lbm.LBM_INIT_REST)
+        lbm.lbm_set_time(gpu_b.h, 13)
+        gpu_b.set_populations(snap)
+        assert np.array_equal(gpu_b.populations(), snap)
+        gpu_a.step(10)
+        gpu_b.step(10)
+        assert gpu_a.time == gpu_b.time == 23
+        assert np.array_equal(gpu_a.populations(), gpu_b.populations())
+        # changing the parity of a live state keeps the canonical populations
+        before = gpu_b.populations()
+        lbm.lbm_set_time(gpu_b.h, 24)
+        assert np.array_equal(gpu_b.populations(), before)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_graph_replay_equals_single_steps(gpu_lib, kind):
+    lbm = gpu_lib
+    shape = (12, 12, 12)
+    u = synthetic.random_solenoidal(12, seed=2)
+    a, _ = make_pair(lbm, shape, nu0=0.002, C=0.13, force_mode=lbm.LBM_FORCE_PAPER_SIN, F0=1e-4, kind=kind)
+    b, _ = make_pair(lbm, shape, nu0=0.002, C=0.13, force_mode=lbm.LBM_FORCE_PAPER_SIN, F0=1e-4, kind=kind)
+    with a, b:
+        a.init(lbm.LBM_INIT_VELOCITY, u=u)
+        b.init(lbm.LBM_INIT_VELOCITY, u=u)
+        a.step(70)          # two captured 32-step graphs + 6 direct launches
+        for _ in range(70):
+            b.step(1)
+        assert np.array_equal(a.populations(), b.populations())
+
+
+def test_direct_and_tma_kernels_agree(gpu_lib):
+    lbm = gpu_lib
+    shape = (16, 24, 40)
+    u = synthetic.random_solenoidal(40, 24, 16, seed=4)
+    out = []
+    for kind in KINDS:
+        g, _ = make_pair(lbm, shape, nu0=0.001, C=0.13, force_mode=lbm.LBM_FORCE_PAPER_SIN, F0=1e-4, kind=kind)
+        with g:
+            g.init(lbm.LBM_INIT_VELOCITY, u=u)
+            g.step(33)
+            out.append(g.populations())
+    assert np.abs(out[0] - out[1]).max() <= 1e-7
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_batch_of_uneven_instances(gpu_lib, kind):
+    """Three instances of different sizes and physics in one handle (one launch
+    per step) match three separate oracle runs."""
+    lbm = gpu_lib
+    specs = [
+        dict(shape=(16, 16, 16), nu0=0.002, C=0.13, fm=lbm.LBM_FORCE_PAPER_SIN, F0=1e-4, body=(0, 0, 0)),
+        dict(shape=(8, 12, 20), nu0=0.01, C=0.0, fm=lbm.LBM_FORCE_CONST, F0=0.0, body=(1e-6, 0, 2e-6)),
+        dict(shape=(5, 6, 7), nu0=0.03, C=0.2, fm=lbm.LBM_FORCE_NONE, F0=0.0, body=(0, 0, 0)),
+    ]
+    params, refs, inits = [], [], []
+    for i, s in enumerate(specs):
+        nz, ny, nx = s["shape"]
+        params.append(lbm.make_params(nx, ny, nz, nu0=s["nu0"], cs=s["C"], f0=s["F0"], body_force=s["body"],
+                                      force_mode=s["fm"], kernel=kind))
+        refs.append(oracle.OracleLBM(nx, ny, nz, s["nu0"], s["C"],
+                                     {0: 0, 1: 1, 2: 2, 3: 3}[s["fm"]], F0=s["F0"], body=s["body"]))
+        inits.append(synthetic.random_solenoidal(nx, ny, nz, seed=20 + i))
+    with lbm.Lattice(params) as g:
+        for i in range(3):
+            g.init(lbm.LBM_INIT_VELOCITY, u=inits[i], inst=i)
+        g.step(21)
+        for i in range(3):
+            refs[i].init_equilibrium(inits[i])
+            refs[i].step(21)
+            assert full_f_rel_error(g.populations(inst=i), refs[i].populations()) <= 1e-5, i
