@@ -244,6 +244,9 @@ def main():
     ap.add_argument("--les-n", type=int, default=100)
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--only-step", action="store_true",
+                    help="time the step kernel only (no e2e, extras or CPU baseline): profiling runs")
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -269,9 +272,18 @@ def main():
     torch.cuda.synchronize()
     cells = n ** 3
     clocks = ClockSampler(local)
-    lat, ms, cfg, st = run_case(lbm, n, 0, 0.0, nu0, args.steps, args.warmup, local, stream, u_dev,
-                                dist, clocks)
+    lat, ms, cfg, st = run_case(lbm, n, args.precision, 0.0, nu0, args.steps, args.warmup, local,
+                                stream, u_dev, dist, clocks)
     assert math.isfinite(st["E_k"]) and st["cells"] == cells, st
+    if args.only_step:
+        if rank == 0:
+            print(json.dumps({"only_step": True, "n": n, "precision": args.precision, "steps": args.steps,
+                              "ms_per_step": ms / args.steps,
+                              "MLUPS": cells * args.steps / (ms * 1e-3) / 1e6,
+                              "GB_s": cells * BYTES_PER_UPDATE[args.precision] * args.steps / (ms * 1e-3) / 1e9,
+                              "kernel": cfg}), flush=True)
+        lat.close()
+        return 0
     # e2e: the public API with host buffers: H2D of the initial field from pinned
     # memory, the K steps, and the D2H statistics read, all inside the timed region
     u_host = u_dev.cpu().pin_memory()

@@ -302,7 +302,7 @@ def lbm_get_fields(h, inst: int, shape) -> dict:
 
 def lbm_get_theta_slice(h, inst: int, axis: int, index: int, shape) -> np.ndarray:
     nz, ny, nx = shape
-    dims = {0: (nz, ny), 1: (nz, nx), 2: (ny, nx)}[axis]
+    dims = {0: (nz, ny), 1: (nz, nx), 2: (ny, nx)}.get(axis, (1,))
     out = np.zeros(dims)
     _check(h, load().lbm_get_theta_slice(h, inst, axis, index, _ptr(out)))
     return out

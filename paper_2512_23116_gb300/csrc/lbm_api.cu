@@ -344,6 +344,7 @@ int run_steps(lbm_t h, int64_t n) {
         cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
         if (rc != LBM_OK) {
           if (g) cudaGraphDestroy(g);
+          (void)cudaGetLastError();  // the invalidated capture; the cause is in h->err
           return rc;
         }
         CK(h, ce);

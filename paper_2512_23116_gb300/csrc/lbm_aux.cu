@@ -252,6 +252,7 @@ int grid_for(int64_t n) {
 template <typename T>
 cudaError_t init_t(const InstDesc& d, bool odd, int mode, double amp, const double* u,
                    int64_t ustride, int64_t c0, int64_t n, cudaStream_t st) {
+  (void)cudaGetLastError();
   k_init<T><<<grid_for(n), kAuxThreads, 0, st>>>(d, odd, mode, amp, u, ustride, c0, n);
   return cudaGetLastError();
 }
@@ -273,6 +274,7 @@ cudaError_t launch_get_pop(const InstDesc& d, int precision, bool odd, int a, do
                            int shifted, int64_t c0, int64_t n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int g = grid_for(n);
+  (void)cudaGetLastError();
   switch (precision) {
     case 0: k_get_pop<float><<<g, kAuxThreads, 0, st>>>(d, odd, a, out, shifted, c0, n); break;
     case 1: k_get_pop<__half><<<g, kAuxThreads, 0, st>>>(d, odd, a, out, shifted, c0, n); break;
@@ -286,6 +288,7 @@ cudaError_t launch_set_pop(const InstDesc& d, int precision, bool odd, int a, co
                            int shifted, int64_t c0, int64_t n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int g = grid_for(n);
+  (void)cudaGetLastError();
   switch (precision) {
     case 0: k_set_pop<float><<<g, kAuxThreads, 0, st>>>(d, odd, a, in, shifted, c0, n); break;
     case 1: k_set_pop<__half><<<g, kAuxThreads, 0, st>>>(d, odd, a, in, shifted, c0, n); break;
@@ -306,6 +309,7 @@ cudaError_t launch_relayout_pair(const InstDesc& d, int precision, bool from_odd
   e = cudaMemcpyAsync(s + plane, base + (size_t)opp(a) * plane, plane, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
   const int g = grid_for((int64_t)d.nx * d.ny * d.nz);
+  (void)cudaGetLastError();
   switch (precision) {
     case 0: k_relayout<float><<<g, kAuxThreads, 0, st>>>(d, from_odd, a, (const float*)s, (const float*)(s + plane)); break;
     case 1: k_relayout<__half><<<g, kAuxThreads, 0, st>>>(d, from_odd, a, (const __half*)s, (const __half*)(s + plane)); break;
@@ -318,12 +322,14 @@ cudaError_t launch_relayout_pair(const InstDesc& d, int precision, bool from_odd
 cudaError_t launch_finish(const double* partials, int ninst, int grid, double* results,
                           double* ring, unsigned long long* seq, int cap, uint32_t* err,
                           cudaStream_t st) {
+  (void)cudaGetLastError();
   k_finish<<<1, 256, 0, st>>>(partials, ninst, grid, results, ring, seq, cap, err);
   return cudaGetLastError();
 }
 
 cudaError_t launch_spec_bin(const void* coeffs, int nx, int ny, int nz, int kmax,
                             double* partials, int blocks, cudaStream_t st) {
+  (void)cudaGetLastError();
   k_spec_bin<<<blocks, kAuxThreads, (size_t)(kmax + 1) * sizeof(double), st>>>(
       static_cast<const float2*>(coeffs), nx, ny, nz, kmax, partials);
   return cudaGetLastError();
@@ -336,12 +342,14 @@ cudaError_t launch_spec_finish(const double* partials, int blocks, int kmax, dou
 
 cudaError_t launch_sum_cols(const double* partials, int rows, int cols, double* out,
                             cudaStream_t st) {
+  (void)cudaGetLastError();
   k_sum_cols<<<(cols + 255) / 256, 256, 0, st>>>(partials, rows, cols, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_struct(const float* u, int nx, int ny, int nz, int r, double* partials,
                           int blocks, cudaStream_t st) {
+  (void)cudaGetLastError();
   k_struct<<<blocks, kAuxThreads, 0, st>>>(u, nx, ny, nz, r, partials);
   return cudaGetLastError();
 }

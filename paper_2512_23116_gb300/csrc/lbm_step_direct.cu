@@ -14,13 +14,17 @@
 
 namespace lbm {
 
+constexpr int kSmemHistBins = 12000;  // (bins + 1) * 4 bytes below 48 KB
+
 template <typename T, bool ODD, int MODE>
 __global__ void __launch_bounds__(256)
 k_step_direct(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64_t tile_hi,
               StatsArgs sa, DiagOut dout) {
   using S = Storage<T>;
   extern __shared__ uint32_t shist[];
-  const bool use_hist = (MODE == MODE_DIAG) && dout.hist != nullptr;
+  // theta histogram in shared memory when it fits the default 48 KB, else
+  // straight into the global counts
+  const bool use_hist = (MODE == MODE_DIAG) && dout.hist != nullptr && dout.hist_bins < kSmemHistBins;
   if (use_hist) {
     for (int i = threadIdx.x; i <= dout.hist_bins; i += blockDim.x) shist[i] = 0u;
     __syncthreads();
@@ -88,7 +92,7 @@ k_step_direct(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, in
         }
       }
       if (MODE != MODE_STEP) acc.add(g, Fx, Fy, Fz, C);
-      if (MODE == MODE_DIAG) diag_write(dout, g, x, y, z, nx, ny, nz, use_hist ? shist : nullptr);
+      if (MODE == MODE_DIAG) diag_write(dout, g, x, y, z, nx, ny, nz, use_hist ? shist : dout.hist);
     }
   }
   if (MODE != MODE_STEP) {
@@ -104,7 +108,10 @@ k_step_direct(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, in
 
 template <typename T, bool ODD, int MODE>
 static cudaError_t launch_direct_t(const LaunchArgs& la, cudaStream_t st) {
-  const size_t smem = (MODE == MODE_DIAG && la.dout.hist) ? (size_t)(la.dout.hist_bins + 1) * 4 : 0;
+  const size_t smem = (MODE == MODE_DIAG && la.dout.hist && la.dout.hist_bins < kSmemHistBins)
+                          ? (size_t)(la.dout.hist_bins + 1) * 4
+                          : 0;
+  (void)cudaGetLastError();  // errors of earlier calls were reported by their return codes
   k_step_direct<T, ODD, MODE><<<la.grid, la.threads, smem, st>>>(la.insts, la.ninst, la.tile_lo,
                                                                    la.tile_hi, la.sa, la.dout);
   return cudaGetLastError();

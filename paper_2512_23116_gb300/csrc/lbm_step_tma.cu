@@ -272,6 +272,7 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
 
 template <typename T, bool ODD, int MODE>
 cudaError_t launch_tma_t(const LaunchArgs& la, cudaStream_t st) {
+  (void)cudaGetLastError();  // errors of earlier calls were reported by their return codes
   k_step_tma<T, ODD, MODE><<<la.grid, la.threads, la.smem_bytes, st>>>(
       la.insts, la.ninst, la.tile_lo, la.tile_hi, la.sa, la.stages, la.tile_bytes_max, la.err);
   return cudaGetLastError();
@@ -314,12 +315,19 @@ cudaError_t launch_step_tma(const LaunchArgs& la, cudaStream_t st) {
 }
 
 cudaError_t tma_prepare(int precision, int smem_bytes) {
+  // The dynamic shared-memory limit is a property of the kernel function,
+  // shared by every handle of the process: only ever raise it.
+  static int granted[3] = {0, 0, 0};
+  if (precision < 0 || precision > 2) return cudaErrorInvalidValue;
+  if (smem_bytes <= granted[precision]) return cudaSuccess;
+  cudaError_t e = cudaErrorInvalidValue;
   switch (precision) {
-    case 0: return set_smem<float>(smem_bytes);
-    case 1: return set_smem<__half>(smem_bytes);
-    case 2: return set_smem<__nv_bfloat16>(smem_bytes);
+    case 0: e = set_smem<float>(smem_bytes); break;
+    case 1: e = set_smem<__half>(smem_bytes); break;
+    case 2: e = set_smem<__nv_bfloat16>(smem_bytes); break;
   }
-  return cudaErrorInvalidValue;
+  if (e == cudaSuccess) granted[precision] = smem_bytes;
+  return e;
 }
 
 int tma_max_blocks_per_sm(int precision, int threads, int smem_bytes) {

@@ -45,3 +45,10 @@ def full_f_rel_error(gpu_shifted, ref_shifted):
 
 def ulp(x: float, mant_bits: int) -> float:
     return 2.0 ** (np.floor(np.log2(x)) - mant_bits)
+
+
+def fp32_mass_tolerance(ncell: int, steps: int, fmax: float) -> float:
+    """Round-off bound on the drift of sum f' with FP32 storage: every step rounds
+    19 ncell stored values by at most ulp/2 with random sign; 6 sigma of that
+    random walk (ulp of the largest |f'|)."""
+    return 6.0 * np.sqrt(19.0 * ncell * (steps + 1)) * 0.5 * ulp(fmax, 23)

@@ -11,17 +11,17 @@ import oracle
 import synthetic
 from oracle import diagnostics as dg
 
-from gpu_helpers import make_pair
+from gpu_helpers import fp32_mass_tolerance, make_pair
 
 pytestmark = pytest.mark.gpu
 
 
-def _les_case(lbm, n=24, steps=30, kind=0, stats_every=0):
+def _les_case(lbm, n=24, steps=30, kind=0, stats_every=0, hist_bins=4096, hist_max=0.02):
     u = synthetic.random_solenoidal(n, seed=1, urms=0.05)
     nu0 = oracle.derive_nu0(0.043, n, 2e3)
     F0 = oracle.forcing_amplitude(0.2, 0.043, n)
     gpu, ref = make_pair(lbm, (n, n, n), nu0=nu0, C=0.13, force_mode=lbm.LBM_FORCE_PAPER_SIN, F0=F0,
-                         kind=kind, stats_every=stats_every, hist_bins=4096, hist_max=0.02)
+                         kind=kind, stats_every=stats_every, hist_bins=hist_bins, hist_max=hist_max)
     gpu.init(lbm.LBM_INIT_VELOCITY, u=u)
     ref.init_equilibrium(u)
     return gpu, ref, nu0
@@ -29,7 +29,8 @@ def _les_case(lbm, n=24, steps=30, kind=0, stats_every=0):
 
 def test_domain_stats_match_oracle(gpu_lib):
     lbm = gpu_lib
-    gpu, ref, nu0 = _les_case(lbm)
+    # this small, strongly sheared case reaches theta ~ 0.05: the histogram covers [0, 0.2)
+    gpu, ref, nu0 = _les_case(lbm, hist_bins=16384, hist_max=0.2)
     with gpu:
         gpu.step(30)
         st = gpu.stats(what=lbm.LBM_STATS_SPECTRUM | lbm.LBM_STATS_STRUCTURE)
@@ -37,18 +38,22 @@ def test_domain_stats_match_oracle(gpu_lib):
     ref.step(30)
     fl = ref.fields()
     F = ref.force_field()
-    want = dg.domain_stats(fl, F, nu0, 0.13, hist_bins=4096, hist_max=0.02)
+    want = dg.domain_stats(fl, F, nu0, 0.13, hist_bins=16384, hist_max=0.2)
     assert st["step"] == 30 and st["cells"] == 24 ** 3
-    assert abs(st["mass"] - want["mass"]) < 1e-7
+    fmax = np.abs(ref.populations()).max()
+    assert abs(st["mass"] - want["mass"]) <= fp32_mass_tolerance(24 ** 3, 30, fmax)
     for k in ("E_k", "eps0", "eps_sgs", "theta_mean", "theta_max", "theta_min", "Kt_mean"):
         assert math.isclose(st[k], want[k], rel_tol=2e-5), (k, st[k], want[k])
     assert math.isclose(st["inj"], want["inj"], rel_tol=1e-4, abs_tol=1e-12)
     for k in ("theta_var", "Kt_var"):
         assert math.isclose(st[k], want[k], rel_tol=1e-3), (k, st[k], want[k])
     assert np.allclose(st["uu"], want["uu"], rtol=2e-5, atol=1e-12)
-    assert np.allclose(st["momentum"], want["momentum"], atol=1e-7)
-    # percentiles: centre of the bin holding the exact percentile (width 0.02/4096)
-    width = 0.02 / 4096
+    # total momentum is zero (sum F = 0); FP32 storage drifts by round-off at the
+    # scale of FP32 precision times the summed magnitude sum |rho u|
+    scale = float(np.sum(np.abs((1.0 + fl["drho"]) * fl["u"])))
+    assert np.abs(np.array(st["momentum"]) - np.array(want["momentum"])).max() <= 2 ** -23 * scale
+    # percentiles: centre of the bin holding the exact percentile (width 0.2/16384)
+    width = 0.2 / 16384
     for p, key in ((5, "theta_p05"), (50, "theta_p50"), (95, "theta_p95"), (99, "theta_p99")):
         assert abs(st[key] - want["theta_p"][p]) <= width, (key, st[key], want["theta_p"][p])
     # spectrum and derived scales
@@ -78,10 +83,12 @@ def test_histogram_counts(gpu_lib):
         h = lbm.lbm_histogram(gpu.h, 0, 4096)
         th = gpu.fields()["theta"]
     assert int(h.sum()) == 16 ** 3
-    idx = np.minimum((th.astype(np.float32) * np.float32(4096 / 0.02)).astype(np.int64), 4095)
-    want = np.bincount(idx.ravel(), minlength=4096)
-    assert np.array_equal(h[:4096], want)
-    assert h[4096] == 0
+    # bin = floor(theta * bins / hist_max) in FP32; theta >= hist_max -> overflow bin
+    q = th.astype(np.float32) * np.float32(4096 / 0.02)
+    idx = np.where(q < 4096, np.floor(q), 4096).astype(np.int64)
+    want = np.bincount(idx.ravel(), minlength=4097)
+    assert np.array_equal(h, want)
+    assert h[4096] > 0  # this LES case has theta above 0.02 somewhere
 
 
 def test_spectrum_single_mode(gpu_lib):
@@ -127,9 +134,14 @@ def test_series_records(gpu_lib):
         while ref.time < r["step"]:
             ref.step(1)
         want = dg.domain_stats(ref.fields(), F, nu0, 0.13)
-        for k in ("E_k", "eps0", "eps_sgs", "theta_mean", "theta_max", "theta_min"):
+        for k in ("E_k", "theta_mean", "theta_max", "theta_min"):
             assert math.isclose(r[k], want[k], rel_tol=2e-5), (r["step"], k)
-        assert abs(r["mass"] - want["mass"]) < 1e-7
+        # eps at t = 0 is the strain of the half-force shift alone (~1e-14): FP32
+        # cancellation in m - m^eq bounds |S| to ~1e-9 absolute
+        for k in ("eps0", "eps_sgs"):
+            assert math.isclose(r[k], want[k], rel_tol=2e-4, abs_tol=1e-12), (r["step"], k)
+        fmax = np.abs(ref.populations()).max()
+        assert abs(r["mass"] - want["mass"]) <= fp32_mass_tolerance(16 ** 3, r["step"], fmax)
 
 
 def test_series_batched_instances(gpu_lib):
