@@ -218,10 +218,15 @@ def time_steps(lbm, lat, stream, steps, warmup, dist):
     return ms
 
 
-def run_case(lbm, n, precision, C, nu0, steps, warmup, device, stream, u_dev, dist, clocks=None):
+def run_case(lbm, n, precision, C, nu0, steps, warmup, device, stream, u_dev, dist, clocks=None,
+             config=""):
     """Create, initialise from the device velocity, time `steps` steps."""
+    kind = rows = stages = threads = 0
+    if config:
+        kind, rows, stages, threads = (int(v) for v in config.split(","))
     p = lbm.make_params(n, precision=precision, nu0=nu0, cs=C, f0=CF * U0 * U0 / n,
-                        force_mode=lbm.LBM_FORCE_PAPER_SIN, device=device, stream=stream.cuda_stream)
+                        force_mode=lbm.LBM_FORCE_PAPER_SIN, device=device, stream=stream.cuda_stream,
+                        kernel=kind, tile_rows=rows, stages=stages, threads=threads)
     lat = lbm.Lattice(p)
     lat.init(lbm.LBM_INIT_VELOCITY, u=u_dev)
     if clocks is not None:
@@ -247,6 +252,8 @@ def main():
     ap.add_argument("--only-step", action="store_true",
                     help="time the step kernel only (no e2e, extras or CPU baseline): profiling runs")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2])
+    ap.add_argument("--config", default="",
+                    help="kind,tile_rows,stages,threads: a fixed kernel configuration (no autotuning)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -273,7 +280,7 @@ def main():
     cells = n ** 3
     clocks = ClockSampler(local)
     lat, ms, cfg, st = run_case(lbm, n, args.precision, 0.0, nu0, args.steps, args.warmup, local,
-                                stream, u_dev, dist, clocks)
+                                stream, u_dev, dist, clocks, config=args.config)
     assert math.isfinite(st["E_k"]) and st["cells"] == cells, st
     if args.only_step:
         if rank == 0:

@@ -99,6 +99,9 @@ typedef struct lbm_params {
   void* stream;           /* cudaStream_t to run on; NULL: the handle creates one */
   int32_t kernel;         /* 0: autotune; 1: direct-load kernel; 2: TMA bulk-copy kernel */
   int32_t tile_rows;      /* rows (of nx cells) per tile; 0: autotune */
+  int32_t stages;         /* TMA pipeline stages; 0: autotune */
+  int32_t threads;        /* threads per block; 0: autotune.  kernel, tile_rows,
+                             stages (TMA) and threads all set: no autotuning */
 } lbm_params;
 
 /* Domain statistics of one instance at one time (all FP64 sums on the device). */

@@ -124,7 +124,8 @@ def domain_stats(fields: dict, F: np.ndarray, nu0: float, C: float,
         "theta_var": float(np.var(th)),
         "theta_min": float(np.min(th)),
         "theta_max": float(np.max(th)),
-        "theta_p": {p: float(np.percentile(th, p)) for p in (5, 50, 95, 99)},
+        # nearest-rank percentile: the ceil(p n)-th smallest value (inverted CDF)
+        "theta_p": {p: float(np.percentile(th, p, method="inverted_cdf")) for p in (5, 50, 95, 99)},
     }
     # K_t = lambda_e / l with lambda_e = (tau_e - 1/2) sqrt(3) dx, l = dx (Eq. Kt_definition).
     kt = math.sqrt(3.0) * th

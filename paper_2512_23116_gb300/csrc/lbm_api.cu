@@ -153,6 +153,11 @@ int validate(const lbm_params& p, std::string& why) {
   if (p.hist_bins < 0 || p.hist_bins > (1 << 16)) { why = "hist_bins out of [0, 65536]"; return LBM_ERR_INVALID_ARG; }
   if (p.kernel < 0 || p.kernel > 2) { why = "unknown kernel kind"; return LBM_ERR_INVALID_ARG; }
   if (p.tile_rows < 0) { why = "tile_rows < 0"; return LBM_ERR_INVALID_ARG; }
+  if (p.stages < 0 || p.stages > 6) { why = "stages out of [0, 6]"; return LBM_ERR_INVALID_ARG; }
+  if (p.threads != 0 && (p.threads < 64 || p.threads > 512 || (p.threads & 31))) {
+    why = "threads must be 0 or a multiple of 32 in [64, 512]";
+    return LBM_ERR_INVALID_ARG;
+  }
   if (!std::isfinite(p.body_force[0]) || !std::isfinite(p.body_force[1]) || !std::isfinite(p.body_force[2])) {
     why = "non-finite body force";
     return LBM_ERR_INVALID_ARG;
@@ -497,7 +502,7 @@ std::vector<int> separations(int n) {
   return r;
 }
 
-int choose_config(lbm_t h, int requested_kind, int requested_rows);
+int choose_config(lbm_t h, const lbm_params& p0);
 
 int alloc_common(lbm_t h) {
   CK(h, cudaMalloc(&h->d_desc, sizeof(InstDesc) * h->inst.size()));
@@ -593,7 +598,7 @@ int create_impl(const lbm_params* params, int count, lbm_t* out) {
     }
     if (e != cudaSuccess) rc = fail(h, LBM_ERR_CUDA, "setup of instance %d: %s", i, cudaGetErrorString(e));
   }
-  if (rc == LBM_OK) rc = choose_config(h, params[0].kernel, params[0].tile_rows);
+  if (rc == LBM_OK) rc = choose_config(h, params[0]);
   if (rc == LBM_OK) {
     // autotuning ran steps on the rest state: restore it and the clock
     for (Inst& I : h->inst) {
@@ -677,10 +682,20 @@ double time_candidate(lbm_t h, int steps) {
   return ms;
 }
 
-int choose_config(lbm_t h, int requested_kind, int requested_rows) {
+int choose_config(lbm_t h, const lbm_params& p0) {
+  const int requested_kind = p0.kernel, requested_rows = p0.tile_rows;
   std::vector<Candidate> cands;
   const int64_t row_stage = max_row_stage_bytes(h);
   const bool tma_ok = row_stage <= 110 * 1024;
+  // a fully specified configuration skips the autotuner
+  if (requested_kind == 1 && requested_rows > 0 && p0.threads > 0)
+    return apply_candidate(h, {1, p0.threads, 0, 0, requested_rows});
+  if (requested_kind == 2 && requested_rows > 0 && p0.threads > 0 && p0.stages > 0) {
+    const int64_t tb = (row_stage * requested_rows + 15) / 16 * 16;
+    if (!tma_ok || (int64_t)p0.stages * tb + 1024 > 227 * 1024)
+      return fail(h, LBM_ERR_UNSUPPORTED, "requested TMA stages do not fit shared memory");
+    return apply_candidate(h, {2, p0.threads, p0.stages, (int)tb, requested_rows});
+  }
   if (requested_kind == 1 || requested_kind == 0)
     cands.push_back({1, 256, 0, 0, requested_rows});
   if ((requested_kind == 2 || requested_kind == 0) && tma_ok) {

@@ -130,3 +130,13 @@ def test_oracle_fields_velocity_is_guo_corrected():
     u = L.fields()["u"]
     F = L.force_field()
     assert np.allclose(u, 0.5 * F, atol=1e-18)
+
+
+def test_percentiles_are_nearest_rank():
+    """theta percentiles are the ceil(p n)-th smallest value (what a histogram's
+    cumulative count locates): for theta = 1..100, p5 = 5, p50 = 50, p99 = 99."""
+    th = np.arange(1.0, 101.0).reshape(4, 5, 5)
+    fl = {"drho": np.zeros_like(th), "u": np.zeros((3, *th.shape)), "snorm": np.zeros_like(th),
+          "theta": th}
+    st = dg.domain_stats(fl, np.zeros((3, *th.shape)), 0.01, 0.1, hist_bins=10, hist_max=200.0)
+    assert st["theta_p"] == {5: 5.0, 50: 50.0, 95: 95.0, 99: 99.0}
