@@ -245,6 +245,28 @@ int lbm_get_params(lbm_t h, int32_t inst, double* nu0, double* s_nu0, double* f0
 int lbm_kernel_config(lbm_t h, int32_t* kind, int32_t* tile_rows, int32_t* stages,
                       int32_t* threads, int32_t* blocks_per_sm);
 
+/* Structure functions S_p(r), p = 1..6, of a velocity field the caller already
+ * holds in device memory, computed without allocating any device memory.  The
+ * paper has no counterpart: it is a service for callers that cannot call
+ * cudaMalloc, such as code sharing the GPU with a framework whose pool
+ * allocator owns the device memory, or pipelines that must not risk the
+ * implicit synchronisation of cudaMalloc / cudaFree.
+ *   u      device, FP32 [3][nz][ny][nx] (x fastest), on the current device
+ *   r      host, nr separations, each >= 1 (periodic wrap)
+ *   sp     device, nr x 6 doubles: sp[k][p-1] = <(u_a(x + r_k e_a) - u_a(x))^p>
+ *          over cells and the three axes, the same quantity as lbm_stats.Sp
+ *   stream cudaStream_t to run on (NULL: the default stream); asynchronous
+ * Limit: 1 <= nr <= 24.  The per-block partial sums live in one fixed array of
+ * 576 KiB of device memory that each GPU loading the library holds until the
+ * process exits; every call shares it, so calls whose work overlaps on the GPU
+ * (other streams, other threads) race and must be serialised by the caller.
+ * The first call on a device looks up that array's address with the device
+ * current; make that first call before any stream capture begins.
+ * Errors: INVALID_ARG (null pointer, extents < 1, nr outside [1, 24], r < 1),
+ * CUDA; lbm_last_error(NULL) gives the text. */
+int lbm_structure_functions_noalloc(const float* u, int32_t nx, int32_t ny, int32_t nz,
+                                    const int32_t* r, int32_t nr, double* sp, void* stream);
+
 /* Text of the last error of `h` (or of the last failed create when h is NULL).
  * The pointer stays valid until the next call on the same handle. */
 const char* lbm_last_error(lbm_t h);

@@ -38,7 +38,7 @@ EXPORTED = [
     "lbm_sync", "lbm_time", "lbm_stats", "lbm_series", "lbm_spectrum", "lbm_histogram",
     "lbm_get_populations", "lbm_set_populations", "lbm_set_time", "lbm_get_fields",
     "lbm_get_theta_slice", "lbm_device_ptr", "lbm_get_params", "lbm_kernel_config",
-    "lbm_last_error", "lbm_version",
+    "lbm_last_error", "lbm_version", "lbm_structure_functions_noalloc",
 ]
 
 
@@ -149,6 +149,8 @@ def load():
         "lbm_kernel_config": ([H] + [ctypes.POINTER(i32)] * 5, ctypes.c_int),
         "lbm_last_error": ([H], ctypes.c_char_p),
         "lbm_version": ([], ctypes.c_char_p),
+        "lbm_structure_functions_noalloc": ([ctypes.c_void_p, i32, i32, i32, ctypes.POINTER(i32), i32,
+                                             ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -328,6 +330,23 @@ def lbm_kernel_config(h) -> dict:
     v = [ctypes.c_int32() for _ in range(5)]
     _check(h, load().lbm_kernel_config(h, *[ctypes.byref(x) for x in v]))
     return dict(zip(("kind", "tile_rows", "stages", "threads", "blocks_per_sm"), [x.value for x in v]))
+
+
+def lbm_structure_functions_noalloc(u, r, sp, stream=None) -> None:
+    """S_p(r) of a device velocity field without any device allocation.
+
+    u: CUDA float32 tensor (3, nz, ny, nx); r: separations (<= 24 of them);
+    sp: CUDA float64 tensor with len(r) * 6 elements, written asynchronously on
+    `stream` (a torch stream, or None for the default stream)."""
+    if u.dtype.itemsize != 4 or not u.is_contiguous() or u.dim() != 4 or u.shape[0] != 3:
+        raise ValueError("u must be a contiguous float32 tensor of shape (3, nz, ny, nx)")
+    if sp.dtype.itemsize != 8 or not sp.is_contiguous():
+        raise ValueError("sp must be a contiguous float64 tensor")
+    _, nz, ny, nx = u.shape
+    ra = (ctypes.c_int32 * max(1, len(r)))(*r)
+    st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    _check(None, load().lbm_structure_functions_noalloc(
+        ctypes.c_void_p(u.data_ptr()), nx, ny, nz, ra, len(r), ctypes.c_void_p(sp.data_ptr()), st))
 
 
 def lbm_last_error(h=None) -> str:

@@ -736,6 +736,11 @@ int choose_config(lbm_t h, const lbm_params& p0) {
 
 }  // namespace
 
+namespace lbm {
+// Error text for entry points that take no handle (read by lbm_last_error(NULL)).
+void set_global_error(const char* msg) { g_create_error = msg; }
+}  // namespace lbm
+
 // ---- public entry points ------------------------------------------------------------
 
 LBM_API int lbm_create(const lbm_params* params, lbm_t* out) { return create_impl(params, 1, out); }
