@@ -633,7 +633,9 @@ int apply_candidate(lbm_t h, const Candidate& c) {
   h->tile_bytes_max = c.tile_bytes;
   h->rows_fixed = c.rows;
   if (c.kind == 2) {
-    h->smem = c.stages * c.tile_bytes + 1024;
+    int max_nx = 1;
+    for (const Inst& I : h->inst) max_nx = std::max(max_nx, I.p.nx);
+    h->smem = tma_smem_bytes(c.stages, c.tile_bytes, max_nx);
     if (tma_prepare(h->precision, h->smem) != cudaSuccess) return LBM_ERR_UNSUPPORTED;
     h->bps = tma_max_blocks_per_sm(h->precision, c.threads, h->smem);
   } else {
@@ -687,32 +689,44 @@ int choose_config(lbm_t h, const lbm_params& p0) {
   std::vector<Candidate> cands;
   const int64_t row_stage = max_row_stage_bytes(h);
   const bool tma_ok = row_stage <= 110 * 1024;
+  int max_nx = 1, min_ny = 1 << 30;
+  for (const Inst& I : h->inst) {
+    max_nx = std::max(max_nx, I.p.nx);
+    min_ny = std::min(min_ny, I.p.ny);
+  }
+  // dynamic shared memory left beside the static reduction scratch of the stats variant
+  const int64_t smem_cap = 220 * 1024;
+  auto fits = [&](int stages, int64_t tb) {
+    return (int64_t)tma_smem_bytes(stages, (int)tb, max_nx) <= smem_cap;
+  };
   // a fully specified configuration skips the autotuner
   if (requested_kind == 1 && requested_rows > 0 && p0.threads > 0)
     return apply_candidate(h, {1, p0.threads, 0, 0, requested_rows});
   if (requested_kind == 2 && requested_rows > 0 && p0.threads > 0 && p0.stages > 0) {
     const int64_t tb = (row_stage * requested_rows + 15) / 16 * 16;
-    if (!tma_ok || (int64_t)p0.stages * tb + 1024 > 227 * 1024)
+    if (!tma_ok || !fits(p0.stages, tb))
       return fail(h, LBM_ERR_UNSUPPORTED, "requested TMA stages do not fit shared memory");
     return apply_candidate(h, {2, p0.threads, p0.stages, (int)tb, requested_rows});
   }
   if (requested_kind == 1 || requested_kind == 0)
     cands.push_back({1, 256, 0, 0, requested_rows});
   if ((requested_kind == 2 || requested_kind == 0) && tma_ok) {
-    const int tile_opts[] = {16 * 1024, 32 * 1024, 48 * 1024, 64 * 1024, 80 * 1024};
+    // a stage holds R x-lines of every population (exact multiples of one row stage)
+    const int row_opts[] = {1, 2, 3, 4, 6, 8, 12, 16};
     const int stage_opts[] = {2, 3, 4};
-    const int thread_opts[] = {256, 512};
-    for (int tb : tile_opts) {
-      if (tb < row_stage) continue;
+    const int thread_opts[] = {256, 384, 512};
+    for (int R : row_opts) {
+      if (requested_rows > 0 && R != requested_rows) continue;
+      if (R > 1 && R > min_ny) break;
+      const int64_t tb = (row_stage * R + 15) / 16 * 16;
+      if (tb > 96 * 1024) break;
       for (int s : stage_opts) {
-        if ((int64_t)s * tb + 1024 > 200 * 1024) continue;
-        for (int th : thread_opts) cands.push_back({2, th, s, tb, requested_rows});
+        if (!fits(s, tb)) continue;
+        for (int th : thread_opts) cands.push_back({2, th, s, (int)tb, R});
       }
     }
-    if (requested_kind == 2 && cands.empty()) {
-      int tb = (int)((row_stage + 15) / 16 * 16);
-      cands.push_back({2, 256, 2, tb, requested_rows});
-    }
+    if (requested_kind == 2 && cands.empty() && fits(2, (row_stage + 15) / 16 * 16))
+      cands.push_back({2, 256, 2, (int)((row_stage + 15) / 16 * 16), 1});
   }
   if (cands.empty())
     return fail(h, LBM_ERR_UNSUPPORTED, "no kernel configuration fits this lattice");

@@ -129,7 +129,7 @@ __device__ __forceinline__ void mrt_collide(float (&f)[19], const float Fx, cons
 
   // ---- macroscopic fields, Eqs. (macroscopic_eq), (guo_velocity) ------------
   const float rho = 1.f + m0;
-  const float irho = 1.f / rho;
+  const float irho = __fdividef(1.f, rho);  // rho ~ 1: the MUFU reciprocal is within 2 ulp
   const float gx = jx + 0.5f * Fx, gy = jy + 0.5f * Fy, gz = jz + 0.5f * Fz;  // rho u
   const float ux = gx * irho, uy = gy * irho, uz = gz * irho;
   const float uxx = ux * ux, uyy = uy * uy, uzz = uz * uz;
@@ -154,9 +154,10 @@ __device__ __forceinline__ void mrt_collide(float (&f)[19], const float Fx, cons
   const float Sxz = -1.5f * s_nu0 * n15;
   const float Syz = -1.5f * s_nu0 * n14;
   const float SS = Sxx * Sxx + Syy * Syy + Szz * Szz + 2.f * (Sxy * Sxy + Sxz * Sxz + Syz * Syz);
-  const float snorm = sqrtf(2.f * SS);          // Eq. (strain_norm)
+  const float SS2 = 2.f * SS;
+  const float snorm = SS2 > 0.f ? SS2 * rsqrtf(SS2) : 0.f;  // Eq. (strain_norm)
   const float theta = 3.f * (nu0 + C * snorm);  // tau_e - 1/2, Eq. (les_viscosity)
-  const float snu = 1.f / (0.5f + theta);
+  const float snu = __fdividef(1.f, 0.5f + theta);
   const float h = 1.f - 0.5f * snu;
 
   // ---- force moments F_m (Eq. meq_fm) --------------------------------------

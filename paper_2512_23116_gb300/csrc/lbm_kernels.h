@@ -31,6 +31,9 @@ cudaError_t launch_step_direct(const LaunchArgs& la, cudaStream_t st);
 int direct_max_blocks_per_sm(int precision, int threads);
 
 cudaError_t launch_step_tma(const LaunchArgs& la, cudaStream_t st);
+// Dynamic shared memory of the TMA kernel: barriers, `stages` tile buffers and
+// the Fz(x) table of the widest instance.
+int tma_smem_bytes(int stages, int tile_bytes, int max_nx);
 int tma_max_blocks_per_sm(int precision, int threads, int smem_bytes);
 cudaError_t tma_prepare(int precision, int smem_bytes);
 

@@ -7,16 +7,25 @@
 //   odd step:  slot opp(a) of rows y - cy_a of plane z - cz_a (a periodic wrap
 //              in y splits a segment in two; the x wrap is resolved in shared
 //              memory because whole lines are loaded).
+// Segment a of the shared-memory tile holds what cell x reads as f_a at
+// position x - [odd] cx_a; the cell writes f*_a into segment opp(a) at position
+// x + [odd] cx_a.  Over the 19 populations the positions a cell writes are the
+// positions it read, so every thread updates its cells in place with no
+// hazard against other threads, and the tile goes back to global memory as
+// the same 19 segments.
+//
 // Each persistent block runs one producer warp and `threads/32 - 1` consumer
-// warps.  The producer streams the segments of the block's next tiles into a
-// ring of `stages` shared-memory buffers with cp.async.bulk (the TMA engine;
-// 16-byte aligned rows, nxp padded for that) and mbarrier transaction counts;
-// consumers read the 19 populations of a cell from shared memory, collide in
-// FP32 registers (lbm_device.cuh), and store the 19 results with coalesced
-// global stores.  A buffer is released to the producer as soon as its
-// consumers have read it.  Every mbarrier wait is bounded by the global timer:
-// on expiry the block records ERR_TIMEOUT, stops issuing, waits (bounded) for
-// its copies in flight and returns.
+// warps.  Producer lane j (j < 19) owns segment j: it streams that segment of
+// the block's next tiles into a ring of `stages` shared-memory buffers with
+// cp.async.bulk (the TMA engine; x-lines start on 16-byte boundaries, nxp is
+// padded for that) completing on mbarrier transaction counts, and writes each
+// finished tile back with cp.async.bulk shared->global (its own bulk group, so
+// it reloads its segment as soon as its own store has read it).  Consumers read the 19
+// populations of a cell from shared memory, collide in FP32 registers
+// (lbm_device.cuh) and write the 19 results back in place; global memory is
+// touched by the TMA engine only.  Every mbarrier wait is bounded by the
+// global timer: on expiry the block records ERR_TIMEOUT, stops issuing, waits
+// (bounded) for its loads in flight and for its stores, and returns.
 #include <cuda_runtime.h>
 
 #include "lbm_device.cuh"
@@ -27,8 +36,14 @@ namespace lbm {
 
 namespace {
 
-constexpr int kBarBytes = 128;          // mbarriers at the start of dynamic smem
+constexpr int kBarBytes = 128;               // mbarriers + abort flag
 constexpr long long kWaitNs = 2000000000ll;  // 2 s per wait
+
+// Per population j: the slot read by the odd step (opp j) and the row shift
+// (cy_j, cz_j), for the producer lanes (one lane per segment).
+__constant__ int8_t c_seg_opp[19] = {1, 0, 3, 2, 5, 4, 7, 6, 9, 8, 11, 10, 13, 12, 15, 14, 17, 16, 18};
+__constant__ int8_t c_seg_cy[19] = {0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 1, -1, 1, -1, 0, 0, 0, 0, 0};
+__constant__ int8_t c_seg_cz[19] = {0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1, 0};
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -82,6 +97,26 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
       : "memory");
 }
 
+__device__ __forceinline__ void bulk_store(void* dst, uint32_t src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+// All committed bulk stores of this thread have finished reading shared memory.
+__device__ __forceinline__ void bulk_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+// All committed bulk stores of this thread are complete (writes performed).
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 struct TileGeom {
   int ii, z, y0, rows;
 };
@@ -97,39 +132,66 @@ __device__ __forceinline__ TileGeom tile_geom(const InstDesc* __restrict__ insts
   return g;
 }
 
-// Producer: issue the 19 (or up to 38, when a y wrap splits a segment) bulk
-// copies of one tile into stage buffer `buf`, completing on mbarrier `bar`.
+// The global rows of segment j of a tile: `first` rows from row ys, then the
+// remaining rows from row 0 of the same plane (periodic wrap in y).
+struct SegRows {
+  const char* plane;  // start of the plane (slot, z) in global memory
+  int ys, first;
+};
+
 template <typename T, bool ODD>
-__device__ __forceinline__ void issue_tile(const InstDesc& d, const TileGeom& g, uint32_t buf,
-                                           uint32_t bar) {
+__device__ __forceinline__ SegRows seg_rows(const InstDesc& d, const TileGeom& g, int j) {
+  const int64_t row_bytes = (int64_t)d.nxp * (int64_t)sizeof(T);
+  const int64_t slot_bytes = d.pop_stride * (int64_t)sizeof(T);
+  const char* base = static_cast<const char*>(d.f);
+  SegRows s;
+  if (!ODD) {
+    s.plane = base + j * slot_bytes + (int64_t)g.z * d.ny * row_bytes;
+    s.ys = g.y0;
+    s.first = g.rows;
+  } else {
+    int zs = g.z - c_seg_cz[j];
+    zs = zs < 0 ? zs + d.nz : (zs >= d.nz ? zs - d.nz : zs);
+    int ys = g.y0 - c_seg_cy[j];
+    ys = ys < 0 ? ys + d.ny : (ys >= d.ny ? ys - d.ny : ys);
+    s.plane = base + c_seg_opp[j] * slot_bytes + (int64_t)zs * d.ny * row_bytes;
+    s.ys = ys;
+    s.first = min(g.rows, d.ny - ys);
+  }
+  return s;
+}
+
+// Producer lane j < 19: the bulk load(s) of segment j of a tile (two when a y
+// wrap splits it).  Lane 0 must have posted the tile's expected bytes.
+template <typename T, bool ODD>
+__device__ __forceinline__ void load_segment(const InstDesc& d, const TileGeom& g, int j, uint32_t buf,
+                                             uint32_t bar) {
   const uint32_t row_bytes = (uint32_t)d.nxp * (uint32_t)sizeof(T);
   const uint32_t seg_bytes = row_bytes * (uint32_t)g.rows;
-  mbar_expect_tx(bar, 19u * seg_bytes);
-  const char* base = static_cast<const char*>(d.f);
-  const int64_t plane_bytes = (int64_t)d.ny * row_bytes;
-  const int64_t slot_bytes = d.pop_stride * (int64_t)sizeof(T);
-#pragma unroll 1
-  for (int j = 0; j < 19; ++j) {
-    const uint32_t dst = buf + (uint32_t)j * seg_bytes;
-    if (!ODD) {
-      const char* src = base + j * slot_bytes + g.z * plane_bytes + (int64_t)g.y0 * row_bytes;
-      bulk_load(dst, src, seg_bytes, bar);
-    } else {
-      const int slot = opp(j);
-      int zs = g.z - cz(j);
-      zs = zs < 0 ? zs + d.nz : (zs >= d.nz ? zs - d.nz : zs);
-      int ys = g.y0 - cy(j);
-      ys = ys < 0 ? ys + d.ny : (ys >= d.ny ? ys - d.ny : ys);
-      const char* plane = base + slot * slot_bytes + zs * plane_bytes;
-      if (ys + g.rows <= d.ny) {
-        bulk_load(dst, plane + (int64_t)ys * row_bytes, seg_bytes, bar);
-      } else {
-        const int first = d.ny - ys;
-        bulk_load(dst, plane + (int64_t)ys * row_bytes, (uint32_t)first * row_bytes, bar);
-        bulk_load(dst + (uint32_t)first * row_bytes, plane, (uint32_t)(g.rows - first) * row_bytes, bar);
-      }
-    }
-  }
+  const SegRows sr = seg_rows<T, ODD>(d, g, j);
+  const uint32_t dst = buf + (uint32_t)j * seg_bytes;
+  bulk_load(dst, sr.plane + (int64_t)sr.ys * row_bytes, (uint32_t)sr.first * row_bytes, bar);
+  if (sr.first < g.rows)
+    bulk_load(dst + (uint32_t)sr.first * row_bytes, sr.plane, (uint32_t)(g.rows - sr.first) * row_bytes, bar);
+}
+
+// Producer lane j < 19: write segment j of a finished tile back to where it was
+// loaded from, as this lane's bulk async-group.
+template <typename T, bool ODD>
+__device__ __forceinline__ void store_segment(const InstDesc& d, const TileGeom& g, int j, uint32_t buf) {
+  const uint32_t row_bytes = (uint32_t)d.nxp * (uint32_t)sizeof(T);
+  const uint32_t seg_bytes = row_bytes * (uint32_t)g.rows;
+  const SegRows sr = seg_rows<T, ODD>(d, g, j);
+  const uint32_t src = buf + (uint32_t)j * seg_bytes;
+  bulk_store(const_cast<char*>(sr.plane) + (int64_t)sr.ys * row_bytes, src, (uint32_t)sr.first * row_bytes);
+  if (sr.first < g.rows)
+    bulk_store(const_cast<char*>(sr.plane), src + (uint32_t)sr.first * row_bytes,
+               (uint32_t)(g.rows - sr.first) * row_bytes);
+  bulk_commit();
+}
+
+__device__ __forceinline__ uint32_t tile_bytes_of(const InstDesc& d, const TileGeom& g, int esize) {
+  return 19u * (uint32_t)d.nxp * (uint32_t)esize * (uint32_t)g.rows;
 }
 
 template <typename T, bool ODD, int MODE>
@@ -141,52 +203,76 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nconsumer_warps = (blockDim.x >> 5) - 1;
   const int nct = nconsumer_warps * 32;
-  const uint32_t bar_full = smem_addr(smem);
-  const uint32_t bar_empty = bar_full + 8u * stages;
+  const uint32_t bar_full = smem_addr(smem);                // stages x 8 B
+  const uint32_t bar_done = bar_full + 8u * stages;          // stages x 8 B
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 16 * stages);
   const uint32_t buf0 = smem_addr(smem + kBarBytes);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 8 * 2 * stages);
+  float* fz_table = reinterpret_cast<float*>(smem + kBarBytes + (size_t)stages * tile_bytes);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) {
       mbar_init(bar_full + 8u * s, 1u);
-      mbar_init(bar_empty + 8u * s, (uint32_t)nconsumer_warps);
+      mbar_init(bar_done + 8u * s, (uint32_t)nconsumer_warps);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    fence_async_smem();
   }
   __syncthreads();
 
   if (warp == nconsumer_warps) {
-    // ---------------- producer warp ----------------
-    if (lane != 0) return;
-    uint32_t outstanding = 0;  // bit s: stage s has a load not yet seen consumed
-    int last_use[8];           // last issued use of each stage
-    for (int s = 0; s < 8; ++s) last_use[s] = -1;
-    int k = 0;
-    for (int64_t t = tile_lo + blockIdx.x; t < tile_hi; t += gridDim.x, ++k) {
-      const int s = k % stages;
-      const int use = k / stages;
-      if (use > 0) {
-        if (!mbar_wait(bar_empty + 8u * s, (uint32_t)((use - 1) & 1))) {
+    // ---------------- producer warp: lane j < 19 issues segment j's bulk copies ----------------
+    const int64_t first = tile_lo + blockIdx.x;
+    const int64_t stride = gridDim.x;
+    const int ntiles = first < tile_hi ? (int)((tile_hi - 1 - first) / stride) + 1 : 0;
+    const bool seg_lane = lane < 19;
+    int loaded = 0;  // tiles whose loads were issued
+    for (; loaded < ntiles && loaded < stages; ++loaded) {
+      const TileGeom g = tile_geom(insts, ninst, first + loaded * stride);
+      const InstDesc& d = insts[g.ii];
+      const uint32_t bar = bar_full + 8u * loaded;
+      if (lane == 0) mbar_expect_tx(bar, tile_bytes_of(d, g, (int)sizeof(T)));
+      __syncwarp();
+      if (seg_lane) load_segment<T, ODD>(d, g, lane, buf0 + (uint32_t)loaded * tile_bytes, bar);
+    }
+    int stored = 0;
+    bool aborted = false;
+    for (; stored < ntiles; ++stored) {
+      const int s = stored % stages;
+      int done_ok = 1;
+      if (lane == 0) done_ok = mbar_wait(bar_done + 8u * s, (uint32_t)((stored / stages) & 1)) ? 1 : 0;
+      done_ok = __shfl_sync(0xffffffffu, done_ok, 0);
+      if (!done_ok) {
+        if (lane == 0) {
           atomicOr(err, ERR_TIMEOUT);
           *abort_flag = 1;
-          break;
         }
-        outstanding &= ~(1u << s);  // its consumers saw the data: that load completed
+        aborted = true;
+        break;
       }
-      if (*abort_flag) break;
-      const TileGeom g = tile_geom(insts, ninst, t);
-      issue_tile<T, ODD>(insts[g.ii], g, buf0 + (uint32_t)s * tile_bytes, bar_full + 8u * s);
-      outstanding |= 1u << s;
-      last_use[s] = use;
+      const TileGeom g = tile_geom(insts, ninst, first + stored * stride);
+      const uint32_t buf = buf0 + (uint32_t)s * tile_bytes;
+      if (seg_lane) store_segment<T, ODD>(insts[g.ii], g, lane, buf);
+      if (loaded < ntiles) {
+        const TileGeom gn = tile_geom(insts, ninst, first + loaded * stride);
+        const InstDesc& dn = insts[gn.ii];
+        const uint32_t bar = bar_full + 8u * s;
+        if (lane == 0) mbar_expect_tx(bar, tile_bytes_of(dn, gn, (int)sizeof(T)));
+        __syncwarp();
+        if (seg_lane) {
+          // this lane's segment region is free once its own store has read it
+          bulk_wait_read_all();
+          load_segment<T, ODD>(dn, gn, lane, buf, bar);
+        }
+        ++loaded;
+      }
     }
-    if (*abort_flag) {
-      // drain: wait (bounded) for every copy still in flight into this block
-      for (int s = 0; s < stages; ++s)
-        if ((outstanding & (1u << s)) && last_use[s] >= 0)
-          (void)mbar_wait(bar_full + 8u * s, (uint32_t)(last_use[s] & 1));
+    if (aborted && lane == 0) {
+      // loads issued but never consumed: wait (bounded) for them to land
+      for (int k = stored; k < loaded; ++k)
+        (void)mbar_wait(bar_full + 8u * (k % stages), (uint32_t)((k / stages) & 1));
     }
+    bulk_wait_all();
     return;
   }
 
@@ -199,72 +285,67 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
   int k = 0;
   for (int64_t t = tile_lo + blockIdx.x; t < tile_hi; t += gridDim.x, ++k) {
     const TileGeom g = tile_geom(insts, ninst, t);
-    if (MODE == MODE_STEP_STATS && g.ii != cur) {
-      if (cur >= 0)
+    const InstDesc& d = insts[g.ii];
+    if (g.ii != cur) {
+      // new instance: flush its predecessor's statistics, reload Fz(x)
+      if (MODE == MODE_STEP_STATS && cur >= 0)
         block_flush(acc, sa.partials + ((int64_t)cur * sa.grid + blockIdx.x) * kNP, nct, 1);
       acc.reset();
+      named_sync(2, nct);
+      for (int x = ctid; x < d.nx; x += nct) fz_table[x] = d.fz_of_x[x] + d.fconst[2];
+      named_sync(2, nct);
       cur = g.ii;
     }
     const int s = k % stages;
-    const int use = k / stages;
     if (ok) {
       if (*abort_flag) {
         ok = false;
-      } else if (!mbar_wait(bar_full + 8u * s, (uint32_t)(use & 1))) {
+      } else if (!mbar_wait(bar_full + 8u * s, (uint32_t)((k / stages) & 1))) {
         atomicOr(err, ERR_TIMEOUT);
         *abort_flag = 1;
         ok = false;
       }
     }
-    if (!ok) {
-      if (MODE == MODE_STEP_STATS) continue;  // keep the named-barrier schedule of the flushes
-      break;
-    }
-    const InstDesc& d = insts[g.ii];
-    const int nx = d.nx, ny = d.ny, nz = d.nz, nxp = d.nxp;
-    const int64_t ps = d.pop_stride;
-    T* __restrict__ fb = static_cast<T*>(d.f);
-    const T* sbuf = reinterpret_cast<const T*>(smem + kBarBytes + (size_t)s * tile_bytes);
+    if (!ok) continue;  // keep the named-barrier schedule of the other consumers
+    const int nx = d.nx, nxp = d.nxp;
+    T* sbuf = reinterpret_cast<T*>(smem + kBarBytes + (size_t)s * tile_bytes);
     const int seg = g.rows * nxp;
     const int ncell = g.rows * nx;
-    const int z = g.z;
-    const int zm = wrap_dec(z, nz), zp = wrap_inc(z, nz);
-    const float Fy = d.fy_of_z[z] + d.fconst[1];
+    const float Fy = d.fy_of_z[g.z] + d.fconst[1];
     const float nu0 = d.nu0, s_nu0 = d.s_nu0, C = d.C;
+    const int dr = nct / nx, dx = nct - dr * nx;
+    int r = ctid / nx, x = ctid - r * nx;
     for (int c = ctid; c < ncell; c += nct) {
-      const int r = c / nx;
-      const int x = c - r * nx;
-      const int y = g.y0 + r;
       const int xm = wrap_dec(x, nx), xp = wrap_inc(x, nx);
+      T* row = sbuf + r * nxp;
       float f[19];
 #pragma unroll
       for (int a = 0; a < 19; ++a) {
         const int xs = ODD ? (cx(a) > 0 ? xm : (cx(a) < 0 ? xp : x)) : x;
-        f[a] = S::cvt(sbuf[a * seg + r * nxp + xs]);
+        f[a] = S::cvt(row[a * seg + xs]);
       }
-      const float Fx = d.fx_of_y[y] + d.fconst[0];
-      const float Fz = d.fz_of_x[x] + d.fconst[2];
+      const float Fx = d.fx_of_y[g.y0 + r] + d.fconst[0];
+      const float Fz = fz_table[x];
       CellDiag cd;
       mrt_collide(f, Fx, Fy, Fz, nu0, s_nu0, C, cd);
-      if (!ODD) {
-        const int64_t o = cell_off(x, y, z, ny, nxp);
 #pragma unroll
-        for (int a = 0; a < 19; ++a) fb[opp(a) * ps + o] = S::pack(f[a]);
-      } else {
-        const int ym = wrap_dec(y, ny), yp = wrap_inc(y, ny);
-#pragma unroll
-        for (int a = 0; a < 19; ++a) {
-          const int xd = cx(a) > 0 ? xp : (cx(a) < 0 ? xm : x);
-          const int yd = cy(a) > 0 ? yp : (cy(a) < 0 ? ym : y);
-          const int zd = cz(a) > 0 ? zp : (cz(a) < 0 ? zm : z);
-          fb[a * ps + cell_off(xd, yd, zd, ny, nxp)] = S::pack(f[a]);
-        }
+      for (int a = 0; a < 19; ++a) {
+        const int xd = ODD ? (cx(a) > 0 ? xp : (cx(a) < 0 ? xm : x)) : x;
+        row[opp(a) * seg + xd] = S::pack(f[a]);
       }
       if (MODE == MODE_STEP_STATS) acc.add(cd, Fx, Fy, Fz, C);
+      x += dx;
+      r += dr;
+      if (x >= nx) {
+        x -= nx;
+        r += 1;
+      }
     }
-    // release the stage to the producer once this warp has read it
+    // hand the tile back: make this warp's shared-memory writes visible to the
+    // TMA engine, then one arrival per warp
+    fence_async_smem();
     __syncwarp();
-    if (lane == 0) mbar_arrive(bar_empty + 8u * s);
+    if (lane == 0) mbar_arrive(bar_done + 8u * s);
   }
   if (MODE == MODE_STEP_STATS && cur >= 0)
     block_flush(acc, sa.partials + ((int64_t)cur * sa.grid + blockIdx.x) * kNP, nct, 1);
@@ -301,6 +382,10 @@ cudaError_t set_smem(int smem) {
 }
 
 }  // namespace
+
+int tma_smem_bytes(int stages, int tile_bytes, int max_nx) {
+  return kBarBytes + stages * tile_bytes + (max_nx * 4 + 15) / 16 * 16;
+}
 
 cudaError_t launch_step_tma(const LaunchArgs& la, cudaStream_t st) {
   if (la.threads < 64 || la.threads > 512 || (la.threads & 31) || la.stages < 1 || la.stages > 6 ||
