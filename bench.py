@@ -192,10 +192,11 @@ def run_reference(args):
     return 0
 
 
-def make_velocity(n, device):
+def make_velocity(n, device, shape=None):
     import synthetic
-    k, a = synthetic.spectrum_coefficients(n, n, n, seed=1, k0=4.0, urms=0.05)
-    return synthetic.synthesize_torch(k, a, n, n, n, device, zchunk=32)
+    nx, ny, nz = shape if shape else (n, n, n)
+    k, a = synthetic.spectrum_coefficients(nx, ny, nz, seed=1, k0=4.0, urms=0.05)
+    return synthetic.synthesize_torch(k, a, nx, ny, nz, device, zchunk=32)
 
 
 def time_steps(lbm, lat, stream, steps, warmup, dist):
@@ -219,12 +220,13 @@ def time_steps(lbm, lat, stream, steps, warmup, dist):
 
 
 def run_case(lbm, n, precision, C, nu0, steps, warmup, device, stream, u_dev, dist, clocks=None,
-             config=""):
+             config="", shape=None):
     """Create, initialise from the device velocity, time `steps` steps."""
     kind = rows = stages = threads = 0
     if config:
         kind, rows, stages, threads = (int(v) for v in config.split(","))
-    p = lbm.make_params(n, precision=precision, nu0=nu0, cs=C, f0=CF * U0 * U0 / n,
+    nx, ny, nz = shape if shape else (n, n, n)
+    p = lbm.make_params(nx, ny, nz, precision=precision, nu0=nu0, cs=C, f0=CF * U0 * U0 / nx,
                         force_mode=lbm.LBM_FORCE_PAPER_SIN, device=device, stream=stream.cuda_stream,
                         kernel=kind, tile_rows=rows, stages=stages, threads=threads)
     lat = lbm.Lattice(p)
@@ -252,6 +254,8 @@ def main():
     ap.add_argument("--only-step", action="store_true",
                     help="time the step kernel only (no e2e, extras or CPU baseline): profiling runs")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2])
+    ap.add_argument("--shape", default="",
+                    help="nx,ny,nz of a non-cubic box for --only-step profiling runs")
     ap.add_argument("--config", default="",
                     help="kind,tile_rows,stages,threads: a fixed kernel configuration (no autotuning)")
     args = ap.parse_args()
@@ -273,18 +277,22 @@ def main():
     lbm.load()
 
     n = args.n
-    nu0 = U0 * n / RE
+    shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else None
+    if shape and not args.only_step:
+        raise SystemExit("--shape is for --only-step profiling runs")
+    nu0 = U0 * (shape[0] if shape else n) / RE
     stream = torch.cuda.Stream(device=dev)
-    u_dev = make_velocity(n, dev)
+    u_dev = make_velocity(n, dev, shape)
     torch.cuda.synchronize()
-    cells = n ** 3
+    cells = shape[0] * shape[1] * shape[2] if shape else n ** 3
     clocks = ClockSampler(local)
     lat, ms, cfg, st = run_case(lbm, n, args.precision, 0.0, nu0, args.steps, args.warmup, local,
-                                stream, u_dev, dist, clocks, config=args.config)
+                                stream, u_dev, dist, clocks, config=args.config, shape=shape)
     assert math.isfinite(st["E_k"]) and st["cells"] == cells, st
     if args.only_step:
         if rank == 0:
-            print(json.dumps({"only_step": True, "n": n, "precision": args.precision, "steps": args.steps,
+            print(json.dumps({"only_step": True, "n": n, "shape": shape, "cells": cells,
+                              "precision": args.precision, "steps": args.steps,
                               "ms_per_step": ms / args.steps,
                               "MLUPS": cells * args.steps / (ms * 1e-3) / 1e6,
                               "GB_s": cells * BYTES_PER_UPDATE[args.precision] * args.steps / (ms * 1e-3) / 1e9,
