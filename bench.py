@@ -241,6 +241,180 @@ def run_case(lbm, n, precision, C, nu0, steps, warmup, device, stream, u_dev, di
     return lat, ms, cfg, st
 
 
+def batch_case(lbm, device, stream, steps, warmup):
+    """48 independent LES instances (12 each of 64^3, 96^3, 100^3, 128^3, seeds
+    1..48, C = 0.13, nu0 from Re = 2e4 at each N, the paper's forcing) in one
+    handle (one launch per step over all instances) against the same 48
+    instances run one after the other as single-instance handles."""
+    import torch
+    sizes = [64] * 12 + [96] * 12 + [100] * 12 + [128] * 12
+    dev = torch.device("cuda", device)
+
+    def params(n):
+        return lbm.make_params(n, nu0=U0 * n / RE, cs=0.13, f0=CF * U0 * U0 / n,
+                               force_mode=lbm.LBM_FORCE_PAPER_SIN, device=device,
+                               stream=stream.cuda_stream)
+
+    def velocity(n, seed):
+        import synthetic
+        k, a = synthetic.spectrum_coefficients(n, n, n, seed=seed, k0=4.0, urms=0.05)
+        return synthetic.synthesize_torch(k, a, n, n, n, dev, zchunk=32)
+
+    cells = sum(n ** 3 for n in sizes)
+    lat = lbm.Lattice([params(n) for n in sizes])
+    for i, n in enumerate(sizes):
+        lat.init(lbm.LBM_INIT_VELOCITY, u=velocity(n, i + 1), inst=i)
+    ms_batch = time_steps(lbm, lat, stream, steps, warmup, False)
+    cfg = lat.config()
+    lat.close()
+    # the same 48 instances as 48 single-instance handles: (a) each run to
+    # completion one after the other (each small lattice then lives in L2),
+    # (b) round robin, one step of every instance per ensemble step
+    ms_seq = 0.0
+    singles = []
+    for i, n in enumerate(sizes):
+        one = lbm.Lattice(params(n))
+        one.init(lbm.LBM_INIT_VELOCITY, u=velocity(n, i + 1))
+        ms_seq += time_steps(lbm, one, stream, steps, warmup, False)
+        singles.append(one)
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(steps):
+        for one in singles:
+            one.step(1)
+    stop.record(stream)
+    stop.synchronize()
+    ms_rr = start.elapsed_time(stop)
+    for one in singles:
+        one.close()
+    return {"instances": len(sizes), "sizes": "12 each of 64^3, 96^3, 100^3, 128^3", "cells": cells,
+            "steps": steps, "MLUPS_batched": cells * steps / (ms_batch * 1e-3) / 1e6,
+            "MLUPS_sequential_to_completion": cells * steps / (ms_seq * 1e-3) / 1e6,
+            "MLUPS_sequential_round_robin": cells * steps / (ms_rr * 1e-3) / 1e6,
+            "speedup_vs_round_robin": ms_rr / ms_batch, "speedup_vs_to_completion": ms_seq / ms_batch,
+            "ms_per_step_batched": ms_batch / steps, "kernel": cfg,
+            "note": "5.09e7 cells, 3.9 GB FP32 batched (HBM); a single instance of 64^3-100^3 "
+                    "fits in L2 when run to completion"}
+
+
+def _dissipation_shell(E, n):
+    """Last shell before E falls below 1e-3 of its peak (bounded by N/3)."""
+    peak = float(np.max(E[1:]))
+    kd = 1
+    for s_ in range(1, min(len(E), n // 3 + 1)):
+        if E[s_] < 1e-3 * peak:
+            break
+        kd = s_
+    return kd
+
+
+def _spectral_error(E, E_ref, n):
+    kd = _dissipation_shell(E_ref, n)
+    rel = np.abs(E[1:kd + 1] - E_ref[1:kd + 1]) / E_ref[1:kd + 1]
+    return {"max_rel_error_shells_1_to_kd": float(rel.max()), "mean_rel_error": float(rel.mean()),
+            "kd": kd}
+
+
+def precision_study(lbm, device, stream, n_small=64, steps_small=500, every_small=50, n_big=800,
+                    steps_big=600, every_big=60):
+    """Spectral error of each storage precision (reading: time-averaged shell
+    spectra, per-shell relative error for shells 1..kd, kd = where E drops below
+    1e-3 of its peak, <= N/3): against the FP64 oracle on an n_small^3 rerun of
+    the setup (C = 0 with nu0 from Re = 2e4, and the LES C = 0.13), and against
+    FP32 storage at n_big^3 (C = 0) over the first 600 steps: from the synthetic
+    initial field (u_rms = 0.05 per component, peaks near 0.3) the C = 0 run at
+    tau - 1/2 = 0.00516 turns unstable at its fastest spot after ~1300 steps in
+    FP32 (earlier with the noisier low-precision storage)."""
+    import torch
+    import oracle
+    import synthetic
+    from oracle import diagnostics as dg
+    out = {}
+    dev = torch.device("cuda", device)
+    m = n_small
+    nu0 = U0 * m / RE
+    F0 = CF * U0 * U0 / m
+    u = synthetic.random_solenoidal(m, seed=1, urms=0.05)
+    kmax = dg.max_shell(m, m, m)
+    for C in (0.0, 0.13):
+        ref = oracle.OracleLBM(m, m, m, nu0, C, oracle.FORCE_PAPER_SIN, F0=F0)
+        ref.init_equilibrium(u)
+        E_ref = np.zeros(kmax + 1)
+        kt_ref = []
+        for _ in range(steps_small // every_small):
+            ref.step(every_small)
+            fl = ref.fields()
+            E_ref += dg.spectrum(fl["u"], kmax)
+            kt_ref.append((np.sqrt(3) * fl["theta"].mean(), 3 * fl["theta"].var()))
+        E_ref /= steps_small // every_small
+        case = {}
+        for prec, name in ((0, "fp32"), (1, "fp16_shifted"), (2, "bf16_shifted")):
+            p = lbm.make_params(m, precision=prec, nu0=nu0, cs=C, f0=F0, force_mode=lbm.LBM_FORCE_PAPER_SIN,
+                                device=device, stream=stream.cuda_stream)
+            try:
+                with lbm.Lattice(p) as L:
+                    L.init(lbm.LBM_INIT_VELOCITY, u=u)
+                    E = np.zeros(kmax + 1)
+                    kt = []
+                    for _ in range(steps_small // every_small):
+                        L.step(every_small)
+                        E += L.spectrum(kmax)
+                        st = L.stats()
+                        kt.append((st["Kt_mean"], st["Kt_var"]))
+                    E /= steps_small // every_small
+            except lbm.LbmError as exc:
+                if exc.code != lbm.LBM_ERR_UNSTABLE:
+                    raise
+                case[name] = {"unstable": True, "non_finite_by_step": (len(kt) + 1) * every_small}
+                continue
+            r = _spectral_error(E, E_ref, m)
+            km, kv = np.mean(kt, axis=0)
+            kmr, kvr = np.mean(kt_ref, axis=0)
+            r["Kt_mean_rel_error"] = float(abs(km - kmr) / kmr)
+            r["Kt_var_rel_error"] = float(abs(kv - kvr) / kvr) if kvr > 0 else None
+            case[name] = r
+        out[f"{m}^3_C{C}_vs_fp64_oracle_{steps_small}_steps"] = case
+    if n_big:
+        nb = n_big
+        nu0b = U0 * nb / RE
+        k, a = synthetic.spectrum_coefficients(nb, nb, nb, seed=1, k0=4.0, urms=0.05)
+        ub = synthetic.synthesize_torch(k, a, nb, nb, nb, dev, zchunk=32)
+        kmax_b = dg.max_shell(nb, nb, nb)
+        spectra = {}
+        for prec, name in ((0, "fp32"), (1, "fp16_shifted"), (2, "bf16_shifted")):
+            p = lbm.make_params(nb, precision=prec, nu0=nu0b, cs=0.0, f0=CF * U0 * U0 / nb,
+                                force_mode=lbm.LBM_FORCE_PAPER_SIN, device=device, stream=stream.cuda_stream)
+            done = 0
+            try:
+                with lbm.Lattice(p) as L:
+                    L.init(lbm.LBM_INIT_VELOCITY, u=ub)
+                    E = np.zeros(kmax_b + 1)
+                    for _ in range(steps_big // every_big):
+                        L.step(every_big)
+                        E += L.spectrum(kmax_b)
+                        L.stats()
+                        done += every_big
+                    spectra[name] = E / (steps_big // every_big)
+            except lbm.LbmError as exc:
+                if exc.code != lbm.LBM_ERR_UNSTABLE:
+                    raise
+                spectra[name] = {"unstable": True, "non_finite_by_step": done + every_big}
+        del ub
+        torch.cuda.empty_cache()
+        res = {}
+        for name in ("fp16_shifted", "bf16_shifted"):
+            if isinstance(spectra["fp32"], dict):
+                res[name] = {"reference": spectra["fp32"], "this": spectra[name] if isinstance(spectra[name], dict) else "finite"}
+            elif isinstance(spectra[name], dict):
+                res[name] = spectra[name]
+            else:
+                res[name] = _spectral_error(spectra[name], spectra["fp32"], nb)
+        out[f"{nb}^3_C0_vs_fp32_{steps_big}_steps"] = res
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -254,6 +428,8 @@ def main():
     ap.add_argument("--only-step", action="store_true",
                     help="time the step kernel only (no e2e, extras or CPU baseline): profiling runs")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2])
+    ap.add_argument("--precision-study", action="store_true",
+                    help="spectral error of FP32/FP16/BF16 storage vs the FP64 oracle (64^3) and vs FP32 (800^3)")
     ap.add_argument("--shape", default="",
                     help="nx,ny,nz of a non-cubic box for --only-step profiling runs")
     ap.add_argument("--config", default="",
@@ -275,6 +451,13 @@ def main():
     __graft_entry__.build()
     import paper_2512_23116_gb300 as lbm
     lbm.load()
+
+    if args.precision_study:
+        stream = torch.cuda.Stream(device=dev)
+        res = precision_study(lbm, local, stream, n_big=args.n)
+        if rank == 0:
+            print(json.dumps({"precision_study": res}), flush=True)
+        return 0
 
     n = args.n
     shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else None
@@ -355,6 +538,8 @@ def main():
             "GB_s": m ** 3 * 152 * 400 / (ms3 * 1e-3) / 1e9, "steps": 400, "C": 0.13, "nu0": nu_les,
             "note": "76 MB lattice: L2-resident (129 MB L2), not an HBM roofline number",
             "kernel": cfg3, "theta_mean": st4["theta_mean"]}
+
+        extra["batch48_les_fp32"] = batch_case(lbm, local, stream, 200, 10)
 
     cpu = None
     if rank == 0:

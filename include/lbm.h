@@ -245,6 +245,17 @@ int lbm_get_params(lbm_t h, int32_t inst, double* nu0, double* s_nu0, double* f0
 int lbm_kernel_config(lbm_t h, int32_t* kind, int32_t* tile_rows, int32_t* stages,
                       int32_t* threads, int32_t* blocks_per_sm);
 
+/* Test hook for the failure path (no counterpart in the paper): the next
+ * TMA-kernel step launch of `h` runs with every device-side wait bounded by
+ * wait_seconds, and block 0 never loads its first tile, so that its consumers'
+ * wait runs out.  The kernel then records LBM_ERR_TIMEOUT, waits (bounded) for
+ * its copies in flight and returns; the next synchronising call reports
+ * LBM_ERR_TIMEOUT and the handle stays usable (re-initialise the state: the
+ * withheld tile was not updated).  Nothing faults or hangs.
+ * Errors: INVALID_ARG (wait_seconds outside (0, 10]), UNSUPPORTED (the handle
+ * runs the direct kernel). */
+int lbm_debug_withhold_load(lbm_t h, double wait_seconds);
+
 /* Structure functions S_p(r), p = 1..6, of a velocity field the caller already
  * holds in device memory, computed without allocating any device memory.  The
  * paper has no counterpart: it is a service for callers that cannot call

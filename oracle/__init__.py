@@ -81,6 +81,7 @@ def _load():
         lib.orc_strain.argtypes = [D, ctypes.c_double, ctypes.c_double, D]
         lib.orc_strain_norm.restype = ctypes.c_double
         lib.orc_strain_norm.argtypes = [D]
+        lib.orc_collide_one.argtypes = [D, D, ctypes.c_double, ctypes.c_double, ctypes.c_int, D, D]
         lib.orc_tau_e.restype = ctypes.c_double
         lib.orc_tau_e.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
         _lib = lib
@@ -168,6 +169,15 @@ def strain_norm(S) -> float:
 
 def tau_e(nu0: float, C: float, S_norm: float) -> float:
     return float(_load().orc_tau_e(float(nu0), float(C), float(S_norm)))
+
+
+def collide_one(fp, F, nu0: float, C: float, fixed_rate: bool = False):
+    """Post-collision f'* (19,) and theta of one cell (Eq. mrt_les_guo)."""
+    out = np.zeros(19)
+    th = np.zeros(1)
+    _load().orc_collide_one(_dp(_vec(fp, 19)), _dp(_vec(F, 3)), float(nu0), float(C),
+                            1 if fixed_rate else 0, _dp(out), _dp(th))
+    return out, float(th[0])
 
 
 # ---- the lattice ------------------------------------------------------------

@@ -412,6 +412,20 @@ static void collide_cell(const orc_lbm* L, const double* fp, const double F[3],
   if (o_theta) *o_theta = tau_e - 0.5;
 }
 
+void orc_collide_one(const double fp[19], const double F[3], double nu0, double C,
+                     int fixed_rate, double fstar[19], double* theta) {
+  orc_lbm L;
+  memset(&L, 0, sizeof L);
+  L.nu0 = nu0;
+  L.C = C;
+  L.s_nu0 = 1.0 / (0.5 + 3.0 * nu0);
+  L.fixed_rate = fixed_rate;
+  orc_lattice(L.c, L.w);
+  orc_moment_matrix(L.M);
+  orc_invert(L.M, L.Minv, 19);
+  collide_cell(&L, fp, F, fstar, NULL, NULL, NULL, theta);
+}
+
 int orc_step(orc_lbm* L, int64_t nsteps, int nthreads) {
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);

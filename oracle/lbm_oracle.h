@@ -60,6 +60,13 @@ double orc_strain_norm(const double S[6]);
  * Delta = dx = 1. */
 double orc_tau_e(double nu0, double C, double S_norm);
 
+/* One collision (Eq. mrt_les_guo, moment space) of a single cell, outside any
+ * lattice: fp = the 19 pre-collision f', F = the force at the cell; returns the
+ * post-collision f'* and, when theta is not NULL, tau_e - 1/2.  fixed_rate = 1
+ * relaxes with the bare rate (no strain). */
+void orc_collide_one(const double fp[19], const double F[3], double nu0, double C,
+                     int fixed_rate, double fstar[19], double* theta);
+
 /* ---- lattice state -------------------------------------------------------- */
 
 typedef struct orc_lbm orc_lbm;

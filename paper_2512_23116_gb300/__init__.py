@@ -38,7 +38,7 @@ EXPORTED = [
     "lbm_sync", "lbm_time", "lbm_stats", "lbm_series", "lbm_spectrum", "lbm_histogram",
     "lbm_get_populations", "lbm_set_populations", "lbm_set_time", "lbm_get_fields",
     "lbm_get_theta_slice", "lbm_device_ptr", "lbm_get_params", "lbm_kernel_config",
-    "lbm_last_error", "lbm_version", "lbm_structure_functions_noalloc",
+    "lbm_last_error", "lbm_version", "lbm_structure_functions_noalloc", "lbm_debug_withhold_load",
 ]
 
 
@@ -151,6 +151,7 @@ def load():
         "lbm_version": ([], ctypes.c_char_p),
         "lbm_structure_functions_noalloc": ([ctypes.c_void_p, i32, i32, i32, ctypes.POINTER(i32), i32,
                                              ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+        "lbm_debug_withhold_load": ([H, ctypes.c_double], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -347,6 +348,10 @@ def lbm_structure_functions_noalloc(u, r, sp, stream=None) -> None:
     st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
     _check(None, load().lbm_structure_functions_noalloc(
         ctypes.c_void_p(u.data_ptr()), nx, ny, nz, ra, len(r), ctypes.c_void_p(sp.data_ptr()), st))
+
+
+def lbm_debug_withhold_load(h, wait_seconds: float) -> None:
+    _check(h, load().lbm_debug_withhold_load(h, float(wait_seconds)))
 
 
 def lbm_last_error(h=None) -> str:

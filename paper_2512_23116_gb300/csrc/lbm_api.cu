@@ -94,6 +94,9 @@ struct lbm_s {
   size_t spec_elems = 0;
   std::map<GraphKey, cudaGraphExec_t> graphs;
   bool use_graphs = true;
+  long long wait_ns = 2000000000ll;  // bound of device-side waits
+  int inject_withhold = 0;           // test hook, consumed by the next TMA step launch
+  long long inject_wait_ns = 0;
   std::string err;
 };
 
@@ -295,12 +298,21 @@ LaunchArgs base_args(lbm_t h) {
   la.smem_bytes = h->smem;
   la.tile_bytes_max = h->tile_bytes_max;
   la.err = h->d_err;
-  la.spin_limit = 1ll << 26;
+  la.wait_ns = h->wait_ns;
+  la.withhold_first_load = 0;
   return la;
 }
 
 cudaError_t launch_step(lbm_t h, const LaunchArgs& la) {
-  return h->kind == 2 ? launch_step_tma(la, h->stream) : launch_step_direct(la, h->stream);
+  if (h->kind != 2) return launch_step_direct(la, h->stream);
+  if (h->inject_withhold) {
+    LaunchArgs li = la;
+    li.withhold_first_load = 1;
+    li.wait_ns = h->inject_wait_ns;
+    h->inject_withhold = 0;
+    return launch_step_tma(li, h->stream);
+  }
+  return launch_step_tma(la, h->stream);
 }
 
 // Enqueue steps t0 .. t0 + n - 1 (no host state change).
@@ -1102,6 +1114,16 @@ LBM_API int lbm_kernel_config(lbm_t h, int32_t* kind, int32_t* tile_rows, int32_
   if (stages) *stages = h->stages;
   if (threads) *threads = h->threads;
   if (blocks_per_sm) *blocks_per_sm = h->bps;
+  return LBM_OK;
+}
+
+LBM_API int lbm_debug_withhold_load(lbm_t h, double wait_seconds) {
+  if (!h) return fail(nullptr, LBM_ERR_INVALID_ARG, "null handle");
+  if (h->kind != 2) return fail(h, LBM_ERR_UNSUPPORTED, "the handle does not run the TMA kernel");
+  if (!(wait_seconds > 0.0) || wait_seconds > 10.0)
+    return fail(h, LBM_ERR_INVALID_ARG, "wait_seconds must be in (0, 10]");
+  h->inject_withhold = 1;
+  h->inject_wait_ns = (long long)(wait_seconds * 1e9);
   return LBM_OK;
 }
 

@@ -154,8 +154,11 @@ __device__ __forceinline__ void mrt_collide(float (&f)[19], const float Fx, cons
   const float Sxz = -1.5f * s_nu0 * n15;
   const float Syz = -1.5f * s_nu0 * n14;
   const float SS = Sxx * Sxx + Syy * Syy + Szz * Szz + 2.f * (Sxy * Sxy + Sxz * Sxz + Syz * Syz);
+  // Eq. (strain_norm).  |S| = SS2 rsqrt(SS2); below 1e-30 (|S| < 1e-15, so
+  // nu_t < 1e-15 for any C <= 1) the strain is taken as zero: the reciprocal
+  // square root of a subnormal is infinite, and 0 x inf would poison theta.
   const float SS2 = 2.f * SS;
-  const float snorm = SS2 > 0.f ? SS2 * rsqrtf(SS2) : 0.f;  // Eq. (strain_norm)
+  const float snorm = SS2 > 1e-30f ? SS2 * rsqrtf(SS2) : 0.f;
   const float theta = 3.f * (nu0 + C * snorm);  // tau_e - 1/2, Eq. (les_viscosity)
   const float snu = __fdividef(1.f, 0.5f + theta);
   const float h = 1.f - 0.5f * snu;
@@ -272,10 +275,12 @@ __device__ __forceinline__ int64_t cell_off(int x, int y, int z, int ny, int nxp
   return ((int64_t)z * ny + y) * nxp + x;
 }
 
-// Index of the instance owning global tile t (tiles are sorted by instance).
+// Index of the instance owning global tile t (tiles are sorted by instance),
+// searching forward from `hint` (a block visits its tiles in increasing order).
 __device__ __forceinline__ int find_instance(const InstDesc* __restrict__ insts, int ninst,
-                                             int64_t t) {
-  int i = 0;
+                                             int64_t t, int hint = 0) {
+  int i = hint < 0 ? 0 : hint;
+  if (i > 0 && t < insts[i].tile_begin) i = 0;
   while (i + 1 < ninst && t >= insts[i].tile_end) ++i;
   return i;
 }

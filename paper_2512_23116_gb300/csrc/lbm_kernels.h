@@ -24,7 +24,8 @@ struct LaunchArgs {
   int smem_bytes;          // dynamic shared memory of the TMA kernel
   int tile_bytes_max;      // bytes of one stage (19 segments)
   uint32_t* err;           // device error word
-  long long spin_limit;    // bounded waits: polls before giving up
+  long long wait_ns;       // bound of every device-side wait (nanoseconds)
+  int withhold_first_load; // test hook: block 0 never loads its first tile
 };
 
 cudaError_t launch_step_direct(const LaunchArgs& la, cudaStream_t st);

@@ -31,9 +31,10 @@ k_step_direct(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, in
   }
   Acc acc;
   acc.reset();
-  int cur = -1;
+  int cur = -1, hint = 0;
   for (int64_t t = tile_lo + blockIdx.x; t < tile_hi; t += gridDim.x) {
-    const int ii = find_instance(insts, ninst, t);
+    const int ii = find_instance(insts, ninst, t, cur < 0 ? hint : cur);
+    hint = ii;
     if (MODE != MODE_STEP && ii != cur) {
       if (cur >= 0)
         block_flush(acc, sa.partials + ((int64_t)cur * sa.grid + blockIdx.x) * kNP, blockDim.x, 0);

@@ -36,8 +36,7 @@ namespace lbm {
 
 namespace {
 
-constexpr int kBarBytes = 128;               // mbarriers + abort flag
-constexpr long long kWaitNs = 2000000000ll;  // 2 s per wait
+constexpr int kBarBytes = 128;  // mbarriers + abort flag
 
 // Per population j: the slot read by the odd step (opp j) and the row shift
 // (cy_j, cz_j), for the producer lanes (one lane per segment).
@@ -80,13 +79,14 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: true when the phase with the given parity has completed.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Bounded wait: true when the phase with the given parity has completed,
+// false once wait_ns nanoseconds of the global timer have passed.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long wait_ns) {
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   while (true) {
     if (mbar_try(bar, parity)) return true;
-    if (global_ns() - t0 > (unsigned long long)kWaitNs) return false;
+    if (global_ns() - t0 > (unsigned long long)wait_ns) return false;
   }
 }
 
@@ -121,9 +121,10 @@ struct TileGeom {
   int ii, z, y0, rows;
 };
 
-__device__ __forceinline__ TileGeom tile_geom(const InstDesc* __restrict__ insts, int ninst, int64_t t) {
+__device__ __forceinline__ TileGeom tile_geom(const InstDesc* __restrict__ insts, int ninst, int64_t t,
+                                              int hint) {
   TileGeom g;
-  g.ii = find_instance(insts, ninst, t);
+  g.ii = find_instance(insts, ninst, t, hint);
   const InstDesc& d = insts[g.ii];
   const int64_t local = t - d.tile_begin;
   g.z = (int)(local / d.tiles_per_plane);
@@ -197,7 +198,8 @@ __device__ __forceinline__ uint32_t tile_bytes_of(const InstDesc& d, const TileG
 template <typename T, bool ODD, int MODE>
 __global__ void __launch_bounds__(512, 1)
 k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64_t tile_hi,
-           StatsArgs sa, int stages, int tile_bytes, uint32_t* __restrict__ err) {
+           StatsArgs sa, int stages, int tile_bytes, uint32_t* __restrict__ err, long long wait_ns,
+           int withhold_first_load) {
   using S = Storage<T>;
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -226,9 +228,15 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
     const int64_t stride = gridDim.x;
     const int ntiles = first < tile_hi ? (int)((tile_hi - 1 - first) / stride) + 1 : 0;
     const bool seg_lane = lane < 19;
+    // test hook: block 0 leaves the barrier of its first tile without an
+    // arrival, so that its consumers' bounded wait runs out
+    const bool withheld = withhold_first_load && blockIdx.x == 0;
     int loaded = 0;  // tiles whose loads were issued
+    int hint_load = 0, hint_store = 0;
     for (; loaded < ntiles && loaded < stages; ++loaded) {
-      const TileGeom g = tile_geom(insts, ninst, first + loaded * stride);
+      if (withheld && loaded == 0) continue;
+      const TileGeom g = tile_geom(insts, ninst, first + loaded * stride, hint_load);
+      hint_load = g.ii;
       const InstDesc& d = insts[g.ii];
       const uint32_t bar = bar_full + 8u * loaded;
       if (lane == 0) mbar_expect_tx(bar, tile_bytes_of(d, g, (int)sizeof(T)));
@@ -240,7 +248,7 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
     for (; stored < ntiles; ++stored) {
       const int s = stored % stages;
       int done_ok = 1;
-      if (lane == 0) done_ok = mbar_wait(bar_done + 8u * s, (uint32_t)((stored / stages) & 1)) ? 1 : 0;
+      if (lane == 0) done_ok = mbar_wait(bar_done + 8u * s, (uint32_t)((stored / stages) & 1), wait_ns) ? 1 : 0;
       done_ok = __shfl_sync(0xffffffffu, done_ok, 0);
       if (!done_ok) {
         if (lane == 0) {
@@ -250,11 +258,13 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
         aborted = true;
         break;
       }
-      const TileGeom g = tile_geom(insts, ninst, first + stored * stride);
+      const TileGeom g = tile_geom(insts, ninst, first + stored * stride, hint_store);
+      hint_store = g.ii;
       const uint32_t buf = buf0 + (uint32_t)s * tile_bytes;
       if (seg_lane) store_segment<T, ODD>(insts[g.ii], g, lane, buf);
       if (loaded < ntiles) {
-        const TileGeom gn = tile_geom(insts, ninst, first + loaded * stride);
+        const TileGeom gn = tile_geom(insts, ninst, first + loaded * stride, hint_load);
+        hint_load = gn.ii;
         const InstDesc& dn = insts[gn.ii];
         const uint32_t bar = bar_full + 8u * s;
         if (lane == 0) mbar_expect_tx(bar, tile_bytes_of(dn, gn, (int)sizeof(T)));
@@ -269,8 +279,10 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
     }
     if (aborted && lane == 0) {
       // loads issued but never consumed: wait (bounded) for them to land
-      for (int k = stored; k < loaded; ++k)
-        (void)mbar_wait(bar_full + 8u * (k % stages), (uint32_t)((k / stages) & 1));
+      for (int k = stored; k < loaded; ++k) {
+        if (withheld && k == 0) continue;
+        (void)mbar_wait(bar_full + 8u * (k % stages), (uint32_t)((k / stages) & 1), wait_ns);
+      }
     }
     bulk_wait_all();
     return;
@@ -284,7 +296,7 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
   bool ok = true;
   int k = 0;
   for (int64_t t = tile_lo + blockIdx.x; t < tile_hi; t += gridDim.x, ++k) {
-    const TileGeom g = tile_geom(insts, ninst, t);
+    const TileGeom g = tile_geom(insts, ninst, t, cur < 0 ? 0 : cur);
     const InstDesc& d = insts[g.ii];
     if (g.ii != cur) {
       // new instance: flush its predecessor's statistics, reload Fz(x)
@@ -300,7 +312,7 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
     if (ok) {
       if (*abort_flag) {
         ok = false;
-      } else if (!mbar_wait(bar_full + 8u * s, (uint32_t)((k / stages) & 1))) {
+      } else if (!mbar_wait(bar_full + 8u * s, (uint32_t)((k / stages) & 1), wait_ns)) {
         atomicOr(err, ERR_TIMEOUT);
         *abort_flag = 1;
         ok = false;
@@ -355,7 +367,8 @@ template <typename T, bool ODD, int MODE>
 cudaError_t launch_tma_t(const LaunchArgs& la, cudaStream_t st) {
   (void)cudaGetLastError();  // errors of earlier calls were reported by their return codes
   k_step_tma<T, ODD, MODE><<<la.grid, la.threads, la.smem_bytes, st>>>(
-      la.insts, la.ninst, la.tile_lo, la.tile_hi, la.sa, la.stages, la.tile_bytes_max, la.err);
+      la.insts, la.ninst, la.tile_lo, la.tile_hi, la.sa, la.stages, la.tile_bytes_max, la.err,
+      la.wait_ns, la.withhold_first_load);
   return cudaGetLastError();
 }
 
@@ -389,7 +402,7 @@ int tma_smem_bytes(int stages, int tile_bytes, int max_nx) {
 
 cudaError_t launch_step_tma(const LaunchArgs& la, cudaStream_t st) {
   if (la.threads < 64 || la.threads > 512 || (la.threads & 31) || la.stages < 1 || la.stages > 6 ||
-      (la.tile_bytes_max & 15))
+      (la.tile_bytes_max & 15) || la.wait_ns <= 0)
     return cudaErrorInvalidValue;
   switch (la.precision) {
     case 0: return dispatch_tma<float>(la, st);

@@ -214,3 +214,25 @@ def test_batch_of_uneven_instances(gpu_lib, kind):
             refs[i].init_equilibrium(inits[i])
             refs[i].step(21)
             assert full_f_rel_error(g.populations(inst=i), refs[i].populations()) <= 1e-5, i
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_subnormal_strain_stays_finite(gpu_lib, kind):
+    """A cell whose non-equilibrium stress is ~1e-20 (its strain norm squared is
+    subnormal in FP32) must collide to finite values that match the oracle (a
+    reciprocal square root of a subnormal once turned such cells into NaN)."""
+    lbm = gpu_lib
+    shape = (4, 4, 4)
+    f = np.zeros((19, *shape))
+    f[6, 1, 2, 3] = f[7, 1, 2, 3] = 5e-21
+    f[8, 1, 2, 3] = f[9, 1, 2, 3] = -5e-21
+    gpu, ref = make_pair(lbm, shape, nu0=0.002, C=0.13, kind=kind)
+    with gpu:
+        gpu.set_populations(f)
+        gpu.step(3)
+        g = gpu.populations()
+        st = gpu.stats()
+    assert np.all(np.isfinite(g)) and np.isfinite(st["theta_max"])
+    ref.set_populations(f.astype(np.float32).astype(np.float64))
+    ref.step(3)
+    assert np.abs(g - ref.populations()).max() <= 1e-24

@@ -245,3 +245,22 @@ def test_streaming_direction():
         # the largest deviation of population a after one step sits at x + c_a
         z, y, x = np.unravel_index(np.argmax(np.abs(g[a])), g[a].shape)
         assert (x, y, z) == ((4 + c[a][0]) % n, (3 + c[a][1]) % n, (2 + c[a][2]) % n)
+
+
+def test_single_cell_collision_matches_the_lattice_step():
+    """orc_collide_one reproduces, cell by cell, the collision inside the lattice
+    step: after one push step, f_a(x + c_a) = f*_a(x)."""
+    c, _ = oracle.lattice()
+    shape = (3, 4, 5)
+    f = _random_state(shape, 8, scale=2e-3)
+    L = oracle.OracleLBM(5, 4, 3, 0.004, 0.13, oracle.FORCE_PAPER_SIN, F0=1e-3)
+    L.set_populations(f)
+    F = L.force_field()
+    L.step(1)
+    g = L.populations()
+    for (z, y, x) in [(0, 0, 0), (1, 2, 3), (2, 3, 4)]:
+        fs, th = oracle.collide_one(f[:, z, y, x], F[:, z, y, x], 0.004, 0.13)
+        for a in range(19):
+            xd, yd, zd = (x + c[a][0]) % 5, (y + c[a][1]) % 4, (z + c[a][2]) % 3
+            assert g[a, zd, yd, xd] == fs[a]
+        assert th >= 3 * 0.004
