@@ -192,6 +192,20 @@ def run_reference(args):
     return 0
 
 
+def aggregate_ranks(ms: float, e2e_ms: float, cells_per_rank: int, steps: int, world: int,
+                    device=None):
+    """Whole-job numbers of a replicas run: the slowest rank's times (MAX over
+    ranks) and the cell updates of all ranks.  Returns (value MLUPS, e2e MLUPS,
+    max ms, max e2e ms).  With world == 1 no collective is called."""
+    import torch
+    t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max, e2e_max = float(t[0]), float(t[1])
+    total = world * cells_per_rank * steps
+    return total / (ms_max * 1e-3) / 1e6, total / (e2e_max * 1e-3) / 1e6, ms_max, e2e_max
+
+
 def make_velocity(n, device, shape=None):
     import synthetic
     nx, ny, nz = shape if shape else (n, n, n)
@@ -415,6 +429,51 @@ def precision_study(lbm, device, stream, n_small=64, steps_small=500, every_smal
     return out
 
 
+def sweep(lbm, device, stream, sizes=(128, 256, 512, 1024), steps=500, warmup=5, err_steps=200):
+    """Roofline sweep: N^3 for each N, FP32 and FP16-shifted storage, the LES
+    setting (C = 0.13, nu0 from Re = 2e4 at each N, the paper's forcing); and
+    the spectral error of both storages against the FP64 oracle at N = 128
+    after err_steps steps."""
+    import torch
+    import oracle
+    from oracle import diagnostics as dg
+    hbm_peak, _ = measured_peaks()
+    rows = []
+    dev = torch.device("cuda", device)
+    for n in sizes:
+        u = make_velocity(n, dev)
+        for prec in (0, 1):
+            p = lbm.make_params(n, precision=prec, nu0=U0 * n / RE, cs=0.13, f0=CF * U0 * U0 / n,
+                                force_mode=lbm.LBM_FORCE_PAPER_SIN, device=device, stream=stream.cuda_stream)
+            with lbm.Lattice(p) as L:
+                L.init(lbm.LBM_INIT_VELOCITY, u=u)
+                ms = time_steps(lbm, L, stream, steps, warmup, False)
+                cfg = L.config()
+            gbs = n ** 3 * BYTES_PER_UPDATE[prec] * steps / (ms * 1e-3) / 1e9
+            rows.append({"N": n, "storage": ["fp32", "fp16_shifted"][prec], "steps": steps,
+                         "MLUPS": n ** 3 * steps / (ms * 1e-3) / 1e6, "GB_s": gbs, "frac_hbm": gbs / hbm_peak,
+                         "kernel": cfg})
+        del u
+        torch.cuda.empty_cache()
+    n = 128
+    u = make_velocity(n, dev).cpu().numpy()
+    ref = oracle.OracleLBM(n, n, n, U0 * n / RE, 0.13, oracle.FORCE_PAPER_SIN, F0=CF * U0 * U0 / n)
+    ref.init_equilibrium(u)
+    ref.step(err_steps)
+    kmax = dg.max_shell(n, n, n)
+    E_ref = dg.spectrum(ref.fields()["u"], kmax)
+    errs = {}
+    for prec in (0, 1):
+        p = lbm.make_params(n, precision=prec, nu0=U0 * n / RE, cs=0.13, f0=CF * U0 * U0 / n,
+                            force_mode=lbm.LBM_FORCE_PAPER_SIN, device=device, stream=stream.cuda_stream)
+        with lbm.Lattice(p) as L:
+            L.init(lbm.LBM_INIT_VELOCITY, u=u)
+            L.step(err_steps)
+            E = L.spectrum(kmax)
+        errs[["fp32", "fp16_shifted"][prec]] = _spectral_error(E, E_ref, n)
+    return {"rows": rows, f"spectral_error_vs_fp64_oracle_128^3_{err_steps}_steps": errs}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -428,6 +487,8 @@ def main():
     ap.add_argument("--only-step", action="store_true",
                     help="time the step kernel only (no e2e, extras or CPU baseline): profiling runs")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2])
+    ap.add_argument("--sweep", action="store_true",
+                    help="roofline sweep N in {128, 256, 512, 1024}, FP32 and FP16, with spectral error at 128^3")
     ap.add_argument("--precision-study", action="store_true",
                     help="spectral error of FP32/FP16/BF16 storage vs the FP64 oracle (64^3) and vs FP32 (800^3)")
     ap.add_argument("--shape", default="",
@@ -452,6 +513,12 @@ def main():
     import paper_2512_23116_gb300 as lbm
     lbm.load()
 
+    if args.sweep:
+        stream = torch.cuda.Stream(device=dev)
+        res = sweep(lbm, local, stream)
+        if rank == 0:
+            print(json.dumps({"sweep": res}), flush=True)
+        return 0
     if args.precision_study:
         stream = torch.cuda.Stream(device=dev)
         res = precision_study(lbm, local, stream, n_big=args.n)
@@ -499,12 +566,7 @@ def main():
     lat.close()
     del u_host
 
-    ms_t = torch.tensor([ms, t_e2e * 1e3], dtype=torch.float64, device=dev)
-    if dist:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_max, e2e_ms = float(ms_t[0]), float(ms_t[1])
-    value = world * cells * args.steps / (ms_max * 1e-3) / 1e6
-    e2e_value = world * cells * args.steps / (e2e_ms * 1e-3) / 1e6
+    value, e2e_value, ms_max, e2e_ms = aggregate_ranks(ms, t_e2e * 1e3, cells, args.steps, world, dev)
 
     hbm_peak, peak_kind = measured_peaks()
     achieved = cells * BYTES_PER_UPDATE[0] * args.steps / (ms * 1e-3) / 1e9  # this rank's kernel

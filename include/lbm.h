@@ -128,6 +128,14 @@ typedef struct lbm_stats_s {
   int32_t r[LBM_MAX_R];
   double Sp[LBM_MAX_R][6];  /* S_p(r) for p = 1..6, three axes pooled */
   double F4[LBM_MAX_R];
+  /* Isotropy (Sec. 3.2, Fig. isotropy_validation) from the fused <u_i u_j>
+   * (the mean flow is zero: the forcing sums to zero over the box):
+   * E_i / E, b_ij = <u_i u_j>/<u_k u_k> - delta_ij/3 (xx, yy, zz, xy, xz, yz),
+   * II_b = -b_ij b_ji / 2, III_b = b_ij b_jk b_ki / 3, and the Lumley
+   * coordinates xi = (III_b/2)^(1/3), eta = (-II_b/3)^(1/2). */
+  double E_frac[3];
+  double b[6];
+  double II_b, III_b, lumley_xi, lumley_eta;
 } lbm_stats_t;
 
 /* One record of the fused in-step statistics (lbm_params.stats_every). */
@@ -193,6 +201,15 @@ int lbm_stats(lbm_t h, int32_t inst, int32_t what, lbm_stats_t* out);
  * since the previous call, oldest first, at most `max` (the device keeps the
  * last 1024).  *count receives the number written.  Synchronous. */
 int lbm_series(lbm_t h, int32_t inst, lbm_record_t* out, int32_t max, int32_t* count);
+
+/* Relative residual of the energy balance of Eq. (energy_balance),
+ * eps = -dE_k/dt + <F.u>, along a record series (lbm_series): for the interior
+ * records k = 1..n-2, residual[k-1] = (eps_k - (-(E_{k+1} - E_{k-1}) /
+ * (t_{k+1} - t_{k-1}) + inj_k)) / eps_k with eps = eps0 + eps_sgs (molecular
+ * plus Smagorinsky dissipation).  `at` (may be NULL) receives the record
+ * times.  Host arithmetic only (no device call).  Errors: INVALID_ARG
+ * (n < 3, null pointers, non-increasing times). */
+int lbm_energy_balance(const lbm_record_t* rec, int32_t n, double* residual, int64_t* at);
 
 /* Energy spectrum E(s), s = 0..kmax, of Eq. (integral_length_scale) with
  * |u_hat|^2, u_hat = N^-3 sum_x u exp(-2 pi i k.x/N), integer shells

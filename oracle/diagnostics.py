@@ -15,6 +15,13 @@ Written from the paper's definitions, one function per quantity:
 * ``derived_scales``      L, eta, lambda, u_rms, eps (Eqs. integral_length_scale -
                           dissipation_rate) and Re_lambda (Sec. 3.1), with the
                           lattice wavenumber k_s = 2 pi s / N.
+* ``isotropy``            directional energy fractions E_i/E, the Reynolds-stress
+                          anisotropy b_ij = <u_i u_j>/<u_k u_k> - delta_ij/3, its
+                          invariants II_b = -b_ij b_ji/2, III_b = b_ij b_jk b_ki/3 and
+                          the Lumley coordinates xi = (III_b/2)^(1/3),
+                          eta = (-II_b/3)^(1/2) (Sec. 3.2, Fig. isotropy_validation).
+* ``energy_balance``      residual of Eq. (energy_balance), eps = -dE_k/dt + <F.u>,
+                          from a time series (central differences).
 
 numpy's FFT is used as a library primitive; a brute-force DFT pins it in
 tests/test_oracle_diagnostics.py.
@@ -154,3 +161,28 @@ def derived_scales(E: np.ndarray, n: int, nu0: float, E_k: float) -> dict:
     lam = math.sqrt(15.0 * nu0 * u_rms * u_rms / eps)
     return {"L": L, "eps": eps, "u_rms": u_rms, "eta": eta, "lambda": lam,
             "Re_lambda": u_rms * lam / nu0}
+
+
+def isotropy(u: np.ndarray) -> dict:
+    """Isotropy diagnostics of a velocity field (3, nz, ny, nx) (Sec. 3.2)."""
+    R = np.array([[np.mean(u[i] * u[j]) for j in range(3)] for i in range(3)])
+    tr = np.trace(R)
+    b = R / tr - np.eye(3) / 3.0
+    II = -0.5 * float(np.sum(b * b.T))
+    III = float(np.einsum("ij,jk,ki->", b, b, b)) / 3.0
+    return {"E_frac": [float(R[i, i] / tr) for i in range(3)],
+            "b": [float(b[0, 0]), float(b[1, 1]), float(b[2, 2]), float(b[0, 1]), float(b[0, 2]),
+                  float(b[1, 2])],
+            "II_b": II, "III_b": III,
+            "xi": float(np.cbrt(III / 2.0)), "eta": float(np.sqrt(max(0.0, -II / 3.0)))}
+
+
+def energy_balance(times, E_k, inj, eps):
+    """Relative residual of Eq. (energy_balance) at the interior samples:
+    (eps - (-dE_k/dt + <F.u>)) / eps with a central difference of E_k."""
+    t = np.asarray(times, dtype=np.float64)
+    E = np.asarray(E_k, dtype=np.float64)
+    dEdt = (E[2:] - E[:-2]) / (t[2:] - t[:-2])
+    rhs = -dEdt + np.asarray(inj, dtype=np.float64)[1:-1]
+    e = np.asarray(eps, dtype=np.float64)[1:-1]
+    return t[1:-1], (e - rhs) / e

@@ -39,6 +39,7 @@ EXPORTED = [
     "lbm_get_populations", "lbm_set_populations", "lbm_set_time", "lbm_get_fields",
     "lbm_get_theta_slice", "lbm_device_ptr", "lbm_get_params", "lbm_kernel_config",
     "lbm_last_error", "lbm_version", "lbm_structure_functions_noalloc", "lbm_debug_withhold_load",
+    "lbm_energy_balance",
 ]
 
 
@@ -72,13 +73,16 @@ class LbmStats(ctypes.Structure):
         ("lambda_", ctypes.c_double), ("u_rms", ctypes.c_double), ("Re_lambda", ctypes.c_double),
         ("nr", ctypes.c_int32), ("r", ctypes.c_int32 * LBM_MAX_R),
         ("Sp", (ctypes.c_double * 6) * LBM_MAX_R), ("F4", ctypes.c_double * LBM_MAX_R),
+        ("E_frac", ctypes.c_double * 3), ("b", ctypes.c_double * 6),
+        ("II_b", ctypes.c_double), ("III_b", ctypes.c_double),
+        ("lumley_xi", ctypes.c_double), ("lumley_eta", ctypes.c_double),
     ]
 
     def as_dict(self) -> dict:
         out = {}
         for name, _ in self._fields_:
             v = getattr(self, name)
-            if name in ("momentum", "uu"):
+            if name in ("momentum", "uu", "E_frac", "b"):
                 v = list(v)
             elif name in ("r", "Sp", "F4"):
                 continue
@@ -152,6 +156,7 @@ def load():
         "lbm_structure_functions_noalloc": ([ctypes.c_void_p, i32, i32, i32, ctypes.POINTER(i32), i32,
                                              ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
         "lbm_debug_withhold_load": ([H, ctypes.c_double], ctypes.c_int),
+        "lbm_energy_balance": ([ctypes.POINTER(LbmRecord), i32, _D, ctypes.POINTER(i64)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -348,6 +353,20 @@ def lbm_structure_functions_noalloc(u, r, sp, stream=None) -> None:
     st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
     _check(None, load().lbm_structure_functions_noalloc(
         ctypes.c_void_p(u.data_ptr()), nx, ny, nz, ra, len(r), ctypes.c_void_p(sp.data_ptr()), st))
+
+
+def lbm_energy_balance(records: list):
+    """(times, relative residuals) of Eq. (energy_balance) along a record series
+    (the dicts of lbm_series)."""
+    n = len(records)
+    buf = (LbmRecord * max(1, n))()
+    for i, r in enumerate(records):
+        buf[i].step = r["step"]
+        buf[i].E_k, buf[i].inj, buf[i].eps0, buf[i].eps_sgs = r["E_k"], r["inj"], r["eps0"], r["eps_sgs"]
+    res = np.zeros(max(1, n - 2))
+    at = (ctypes.c_int64 * max(1, n - 2))()
+    _check(None, load().lbm_energy_balance(buf, n, _ptr(res), at))
+    return np.array(list(at)[:n - 2]), res[:n - 2]
 
 
 def lbm_debug_withhold_load(h, wait_seconds: float) -> None:

@@ -462,6 +462,28 @@ void fill_from_sums(lbm_stats_t* out, const double* r, const Inst& I, int64_t t)
   // Eq. (Kt_definition): K_t = (tau_e - 1/2) sqrt(3) dx / l with l = dx.
   out->Kt_mean = std::sqrt(3.0) * out->theta_mean;
   out->Kt_var = 3.0 * out->theta_var;
+  // isotropy of the Reynolds stresses (Sec. 3.2): b_ij, its invariants, Lumley (xi, eta)
+  const double tr = out->uu[0] + out->uu[1] + out->uu[2];
+  if (tr > 0.0) {
+    double B[3][3];
+    const int ij[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+    for (int k = 0; k < 6; ++k) {
+      const int i = ij[k][0], j = ij[k][1];
+      B[i][j] = B[j][i] = out->uu[k] / tr - (i == j ? 1.0 / 3.0 : 0.0);
+      out->b[k] = B[i][j];
+    }
+    for (int i = 0; i < 3; ++i) out->E_frac[i] = out->uu[i] / tr;
+    double bb = 0.0, bbb = 0.0;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        bb += B[i][j] * B[j][i];
+        for (int k = 0; k < 3; ++k) bbb += B[i][j] * B[j][k] * B[k][i];
+      }
+    out->II_b = -0.5 * bb;
+    out->III_b = bbb / 3.0;
+    out->lumley_xi = std::cbrt(out->III_b / 2.0);
+    out->lumley_eta = std::sqrt(std::max(0.0, -out->II_b / 3.0));
+  }
 }
 
 // Exact integer shell s with s - 1/2 <= sqrt(K) < s + 1/2.
@@ -958,6 +980,22 @@ LBM_API int lbm_series(lbm_t h, int32_t inst, lbm_record_t* out, int32_t max, in
     o.theta_max = s.theta_max;
     ++*count;
     I.rec_read = k + 1;
+  }
+  return LBM_OK;
+}
+
+LBM_API int lbm_energy_balance(const lbm_record_t* rec, int32_t n, double* residual, int64_t* at) {
+  if (!rec || !residual || n < 3)
+    return fail(nullptr, LBM_ERR_INVALID_ARG, "energy balance needs >= 3 records and outputs");
+  for (int k = 1; k < n; ++k)
+    if (rec[k].step <= rec[k - 1].step)
+      return fail(nullptr, LBM_ERR_INVALID_ARG, "record times must increase");
+  for (int k = 1; k + 1 < n; ++k) {
+    // Eq. (energy_balance): eps = -dE_k/dt + <F.u>, central difference in time
+    const double dEdt = (rec[k + 1].E_k - rec[k - 1].E_k) / (double)(rec[k + 1].step - rec[k - 1].step);
+    const double eps = rec[k].eps0 + rec[k].eps_sgs;
+    residual[k - 1] = (eps - (-dEdt + rec[k].inj)) / eps;
+    if (at) at[k - 1] = rec[k].step;
   }
   return LBM_OK;
 }

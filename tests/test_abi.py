@@ -54,7 +54,8 @@ int main(void) {
   printf("%zu %zu %zu\n", sizeof(lbm_params), sizeof(lbm_stats_t), sizeof(lbm_record_t));
   printf("%zu %zu %zu %zu\n", offsetof(lbm_params, stream), offsetof(lbm_params, tile_rows),
          offsetof(lbm_params, hist_max), offsetof(lbm_params, body_force));
-  printf("%zu %zu %zu\n", offsetof(lbm_stats_t, nr), offsetof(lbm_stats_t, Sp), offsetof(lbm_stats_t, F4));
+  printf("%zu %zu %zu %zu\n", offsetof(lbm_stats_t, nr), offsetof(lbm_stats_t, Sp), offsetof(lbm_stats_t, F4),
+         offsetof(lbm_stats_t, lumley_eta));
   return 0;
 }
 '''
@@ -71,7 +72,7 @@ int main(void) {
     assert offs == [P.stream.offset, P.tile_rows.offset, P.hist_max.offset, P.body_force.offset]
     offs = [int(v) for v in lines[2].split()]
     S = lib.LbmStats
-    assert offs == [S.nr.offset, S.Sp.offset, S.F4.offset]
+    assert offs == [S.nr.offset, S.Sp.offset, S.F4.offset, S.lumley_eta.offset]
 
 
 @pytest.mark.parametrize("kw,frag", [
@@ -107,3 +108,23 @@ def test_no_device_is_an_error_not_a_fallback(lib):
     with pytest.raises(lib.LbmError) as ei:
         lib.lbm_create(lib.make_params(8, nu0=0.01))
     assert ei.value.code == lib.LBM_ERR_CUDA
+
+
+def test_energy_balance_host_function(lib):
+    """lbm_energy_balance is host arithmetic: runs without a GPU.  An exactly
+    balanced synthetic series (E = E0 exp(-2at), eps = 2aE + I) gives residuals
+    within the O(dt^2) central-difference error; bad input is rejected."""
+    import numpy as np
+
+    a, E0, I = 1e-3, 2e-3, 3e-7
+    recs = []
+    for t in range(0, 2000, 50):
+        E = E0 * np.exp(-2 * a * t)
+        recs.append({"step": t, "E_k": E, "inj": I, "eps0": 2 * a * E + I, "eps_sgs": 0.0})
+    at, r = lib.lbm_energy_balance(recs)
+    assert list(at) == list(range(50, 1950, 50))
+    assert np.abs(r).max() < 2 * (2 * a * 50) ** 2 / 6
+    with pytest.raises(lib.LbmError):
+        lib.lbm_energy_balance(recs[:2])
+    with pytest.raises(lib.LbmError):
+        lib.lbm_energy_balance([recs[1], recs[0], recs[2]])

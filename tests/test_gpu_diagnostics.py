@@ -72,6 +72,12 @@ def test_domain_stats_match_oracle(gpu_lib):
         assert np.allclose(st["Sp"][:, p - 1], sf["S"][:, p], rtol=1e-4)
     assert np.allclose(st["F4"], sf["F4"], rtol=1e-4)
     assert np.all(np.abs(st["Sp"][:, 0]) < 1e-9)  # S1 = 0 on a periodic box
+    # isotropy (Sec. 3.2) from the fused <u_i u_j>
+    iso = dg.isotropy(fl["u"])
+    assert np.allclose(st["E_frac"], iso["E_frac"], rtol=2e-5)
+    assert np.allclose(st["b"], iso["b"], atol=2e-6)
+    for k, kk in (("II_b", "II_b"), ("III_b", "III_b"), ("lumley_xi", "xi"), ("lumley_eta", "eta")):
+        assert math.isclose(st[k], iso[kk], rel_tol=1e-3, abs_tol=1e-7), (k, st[k], iso[kk])
 
 
 def test_histogram_counts(gpu_lib):
@@ -207,3 +213,30 @@ def test_invalid_calls_on_a_live_handle(gpu_lib):
             assert ei.value.code == lbm.LBM_ERR_INVALID_ARG
         gpu.step(1)
         gpu.sync()
+
+
+def test_energy_balance_series_matches_oracle(gpu_lib):
+    """Residual of Eq. (energy_balance) along the fused in-step records of a
+    forced LES run (stats every 20 steps), against the same residual from the
+    oracle's states."""
+    lbm = gpu_lib
+    n = 24
+    gpu, ref, nu0 = _les_case(lbm, n=n, stats_every=20)
+    with gpu:
+        gpu.step(200)
+        recs = gpu.series()
+    assert [r["step"] for r in recs] == list(range(0, 200, 20))
+    at, res = lbm.lbm_energy_balance(recs)
+    F = ref.force_field()
+    E, inj, eps, times = [], [], [], []
+    for t in range(0, 200, 20):
+        while ref.time < t:
+            ref.step(1)
+        d = dg.domain_stats(ref.fields(), F, nu0, 0.13)
+        times.append(t)
+        E.append(d["E_k"])
+        inj.append(d["inj"])
+        eps.append(d["eps0"] + d["eps_sgs"])
+    t_ref, r_ref = dg.energy_balance(times, E, inj, eps)
+    assert list(at) == list(t_ref)
+    assert np.allclose(res, r_ref, atol=1e-4), (res, r_ref)

@@ -140,3 +140,52 @@ def test_percentiles_are_nearest_rank():
           "theta": th}
     st = dg.domain_stats(fl, np.zeros((3, *th.shape)), 0.01, 0.1, hist_bins=10, hist_max=200.0)
     assert st["theta_p"] == {5: 5.0, 50: 50.0, 95: 95.0, 99: 99.0}
+
+
+def test_isotropy_lumley_vertices():
+    """Textbook vertices of the Lumley triangle: one-component turbulence at
+    (xi, eta) = (1/3, 1/3); an isotropic random field near the origin."""
+    rng = np.random.default_rng(4)
+    n = 16
+    u = np.zeros((3, n, n, n))
+    u[0] = rng.normal(size=(n, n, n))
+    iso = dg.isotropy(u)
+    assert np.allclose(iso["E_frac"], [1, 0, 0], atol=1e-15)
+    assert np.allclose(iso["b"], [2 / 3, -1 / 3, -1 / 3, 0, 0, 0], atol=1e-12)
+    assert math.isclose(iso["II_b"], -1 / 3, rel_tol=1e-12)
+    assert math.isclose(iso["III_b"], 2 / 27, rel_tol=1e-12)
+    assert math.isclose(iso["xi"], 1 / 3, rel_tol=1e-12) and math.isclose(iso["eta"], 1 / 3, rel_tol=1e-12)
+    iso = dg.isotropy(synthetic_isotropic(24))
+    assert abs(iso["xi"]) < 0.1 and iso["eta"] < 0.1
+
+
+def synthetic_isotropic(n):
+    import synthetic
+    return synthetic.random_solenoidal(n, seed=9)
+
+
+def test_two_component_axisymmetric_vertex_exact():
+    """u_x and u_y with equal variance and zero correlation, u_z = 0:
+    b = diag(1/6, 1/6, -1/3), II_b = -1/12, III_b = -1/108, (xi, eta) = (-1/6, 1/6)."""
+    n = 8
+    x = np.arange(n)
+    u = np.zeros((3, n, n, n))
+    u[0] = np.sin(2 * np.pi * x / n)[None, None, :]
+    u[1] = np.cos(2 * np.pi * x / n)[None, None, :]
+    iso = dg.isotropy(u)
+    assert np.allclose(iso["b"], [1 / 6, 1 / 6, -1 / 3, 0, 0, 0], atol=1e-12)
+    assert math.isclose(iso["II_b"], -1 / 12, rel_tol=1e-12)
+    assert math.isclose(iso["III_b"], -1 / 108, rel_tol=1e-12)
+    assert math.isclose(iso["xi"], -1 / 6, rel_tol=1e-12) and math.isclose(iso["eta"], 1 / 6, rel_tol=1e-12)
+
+
+def test_energy_balance_closed_form():
+    """E_k(t) = E0 exp(-2 a t) with constant injection I and eps = 2 a E + I
+    balances exactly up to the central-difference error O(dt^2)."""
+    a, E0, I = 1e-3, 2e-3, 3e-7
+    t = np.arange(0, 2000, 50.0)
+    E = E0 * np.exp(-2 * a * t)
+    eps = 2 * a * E + I
+    tc, r = dg.energy_balance(t, E, np.full_like(t, I), eps)
+    # central difference of exp(-2at) overestimates |dE/dt| by (2 a dt)^2 / 6
+    assert np.abs(r).max() < 2 * (2 * a * 50) ** 2 / 6 + 1e-12
