@@ -234,7 +234,7 @@ def time_steps(lbm, lat, stream, steps, warmup, dist):
 
 
 def run_case(lbm, n, precision, C, nu0, steps, warmup, device, stream, u_dev, dist, clocks=None,
-             config="", shape=None):
+             config="", shape=None, row_align=0):
     """Create, initialise from the device velocity, time `steps` steps."""
     kind = rows = stages = threads = 0
     if config:
@@ -242,7 +242,7 @@ def run_case(lbm, n, precision, C, nu0, steps, warmup, device, stream, u_dev, di
     nx, ny, nz = shape if shape else (n, n, n)
     p = lbm.make_params(nx, ny, nz, precision=precision, nu0=nu0, cs=C, f0=CF * U0 * U0 / nx,
                         force_mode=lbm.LBM_FORCE_PAPER_SIN, device=device, stream=stream.cuda_stream,
-                        kernel=kind, tile_rows=rows, stages=stages, threads=threads)
+                        kernel=kind, tile_rows=rows, stages=stages, threads=threads, row_align=row_align)
     lat = lbm.Lattice(p)
     lat.init(lbm.LBM_INIT_VELOCITY, u=u_dev)
     if clocks is not None:
@@ -484,6 +484,9 @@ def main():
     ap.add_argument("--les-n", type=int, default=100)
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--row-align", type=int, default=0, help="x-line alignment in bytes (lbm_params.row_align)")
+    ap.add_argument("--cs", type=float, default=0.0,
+                    help="Smagorinsky constant of an --only-step run (the DNS shape uses 0)")
     ap.add_argument("--only-step", action="store_true",
                     help="time the step kernel only (no e2e, extras or CPU baseline): profiling runs")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2])
@@ -536,8 +539,10 @@ def main():
     torch.cuda.synchronize()
     cells = shape[0] * shape[1] * shape[2] if shape else n ** 3
     clocks = ClockSampler(local)
-    lat, ms, cfg, st = run_case(lbm, n, args.precision, 0.0, nu0, args.steps, args.warmup, local,
-                                stream, u_dev, dist, clocks, config=args.config, shape=shape)
+    lat, ms, cfg, st = run_case(lbm, n, args.precision, args.cs if args.only_step else 0.0, nu0,
+                                args.steps, args.warmup, local,
+                                stream, u_dev, dist, clocks, config=args.config, shape=shape,
+                                row_align=args.row_align)
     assert math.isfinite(st["E_k"]) and st["cells"] == cells, st
     if args.only_step:
         if rank == 0:

@@ -102,6 +102,9 @@ typedef struct lbm_params {
   int32_t stages;         /* TMA pipeline stages; 0: autotune */
   int32_t threads;        /* threads per block; 0: autotune.  kernel, tile_rows,
                              stages (TMA) and threads all set: no autotuning */
+  int32_t row_align;      /* byte alignment of each x-line (power of two >= 16;
+                             0: 16).  Padding costs memory, not bandwidth: only
+                             the nx live cells of a line are moved */
 } lbm_params;
 
 /* Domain statistics of one instance at one time (all FP64 sums on the device). */

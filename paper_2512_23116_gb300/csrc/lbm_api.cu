@@ -156,6 +156,10 @@ int validate(const lbm_params& p, std::string& why) {
   if (p.hist_bins < 0 || p.hist_bins > (1 << 16)) { why = "hist_bins out of [0, 65536]"; return LBM_ERR_INVALID_ARG; }
   if (p.kernel < 0 || p.kernel > 2) { why = "unknown kernel kind"; return LBM_ERR_INVALID_ARG; }
   if (p.tile_rows < 0) { why = "tile_rows < 0"; return LBM_ERR_INVALID_ARG; }
+  if (p.row_align != 0 && (p.row_align < 16 || p.row_align > 65536 || (p.row_align & (p.row_align - 1)))) {
+    why = "row_align must be 0 or a power of two in [16, 65536]";
+    return LBM_ERR_INVALID_ARG;
+  }
   if (p.stages < 0 || p.stages > 6) { why = "stages out of [0, 6]"; return LBM_ERR_INVALID_ARG; }
   if (p.threads != 0 && (p.threads < 64 || p.threads > 512 || (p.threads & 31))) {
     why = "threads must be 0 or a multiple of 32 in [64, 512]";
@@ -179,7 +183,9 @@ void derive(Inst& I) {
   I.C = p.cs;
   I.hist_bins = p.hist_bins > 0 ? p.hist_bins : 4096;
   I.hist_max = p.hist_max > 0.0 ? p.hist_max : 0.02;
-  I.nxp = (p.nx + elems_per_16b(p.precision) - 1) / elems_per_16b(p.precision) * elems_per_16b(p.precision);
+  const int esz = p.precision == LBM_FP32 ? 4 : 2;
+  const int align_elems = std::max(elems_per_16b(p.precision), (p.row_align > 0 ? p.row_align : 16) / esz);
+  I.nxp = (p.nx + align_elems - 1) / align_elems * align_elems;
   I.ncell = (int64_t)p.nx * p.ny * p.nz;
 }
 
@@ -262,6 +268,10 @@ int build_tiles(lbm_t h) {
     d.ny = p.ny;
     d.nz = p.nz;
     d.nxp = I.nxp;
+    {
+      const int e16 = elems_per_16b(h->precision);
+      d.row_copy_bytes = (p.nx + e16 - 1) / e16 * e16 * (int)h->esize;
+    }
     d.pop_stride = (int64_t)p.nz * p.ny * I.nxp;
     d.rows = R;
     d.tiles_per_plane = tpp;

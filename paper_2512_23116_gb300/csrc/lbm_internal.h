@@ -16,7 +16,8 @@ struct InstDesc {
   float nu0;               // bare viscosity
   float s_nu0;             // bare shear rate 1/(1/2 + 3 nu0)
   float C;                 // Smagorinsky constant
-  int32_t nx, ny, nz, nxp; // nxp: x stride (nx rounded up to 16 bytes)
+  int32_t nx, ny, nz, nxp; // nxp: x stride (nx rounded up to the row alignment)
+  int32_t row_copy_bytes;  // bytes of one x-line a bulk copy moves (nx cells, 16-byte multiple)
   int64_t pop_stride;      // nz * ny * nxp
   int32_t rows;            // rows (y lines of nx cells) per tile
   int32_t tiles_per_plane; // ceil(ny / rows)

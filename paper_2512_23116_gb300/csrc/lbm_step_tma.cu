@@ -162,8 +162,10 @@ __device__ __forceinline__ SegRows seg_rows(const InstDesc& d, const TileGeom& g
   return s;
 }
 
-// Producer lane j < 19: the bulk load(s) of segment j of a tile (two when a y
-// wrap splits it).  Lane 0 must have posted the tile's expected bytes.
+// Producer lane j < 19: the bulk load(s) of segment j of a tile.  Without
+// padding a segment is one contiguous run (two when a y wrap splits it); with
+// padded x-lines every line is copied on its own, live cells only.  Lane 0
+// must have posted the tile's expected bytes.
 template <typename T, bool ODD>
 __device__ __forceinline__ void load_segment(const InstDesc& d, const TileGeom& g, int j, uint32_t buf,
                                              uint32_t bar) {
@@ -171,9 +173,16 @@ __device__ __forceinline__ void load_segment(const InstDesc& d, const TileGeom& 
   const uint32_t seg_bytes = row_bytes * (uint32_t)g.rows;
   const SegRows sr = seg_rows<T, ODD>(d, g, j);
   const uint32_t dst = buf + (uint32_t)j * seg_bytes;
-  bulk_load(dst, sr.plane + (int64_t)sr.ys * row_bytes, (uint32_t)sr.first * row_bytes, bar);
-  if (sr.first < g.rows)
-    bulk_load(dst + (uint32_t)sr.first * row_bytes, sr.plane, (uint32_t)(g.rows - sr.first) * row_bytes, bar);
+  if ((uint32_t)d.row_copy_bytes == row_bytes) {
+    bulk_load(dst, sr.plane + (int64_t)sr.ys * row_bytes, (uint32_t)sr.first * row_bytes, bar);
+    if (sr.first < g.rows)
+      bulk_load(dst + (uint32_t)sr.first * row_bytes, sr.plane, (uint32_t)(g.rows - sr.first) * row_bytes, bar);
+  } else {
+    for (int r = 0; r < g.rows; ++r) {
+      const int y = r < sr.first ? sr.ys + r : r - sr.first;
+      bulk_load(dst + (uint32_t)r * row_bytes, sr.plane + (int64_t)y * row_bytes, (uint32_t)d.row_copy_bytes, bar);
+    }
+  }
 }
 
 // Producer lane j < 19: write segment j of a finished tile back to where it was
@@ -184,15 +193,26 @@ __device__ __forceinline__ void store_segment(const InstDesc& d, const TileGeom&
   const uint32_t seg_bytes = row_bytes * (uint32_t)g.rows;
   const SegRows sr = seg_rows<T, ODD>(d, g, j);
   const uint32_t src = buf + (uint32_t)j * seg_bytes;
-  bulk_store(const_cast<char*>(sr.plane) + (int64_t)sr.ys * row_bytes, src, (uint32_t)sr.first * row_bytes);
-  if (sr.first < g.rows)
-    bulk_store(const_cast<char*>(sr.plane), src + (uint32_t)sr.first * row_bytes,
-               (uint32_t)(g.rows - sr.first) * row_bytes);
+  if ((uint32_t)d.row_copy_bytes == row_bytes) {
+    bulk_store(const_cast<char*>(sr.plane) + (int64_t)sr.ys * row_bytes, src, (uint32_t)sr.first * row_bytes);
+    if (sr.first < g.rows)
+      bulk_store(const_cast<char*>(sr.plane), src + (uint32_t)sr.first * row_bytes,
+                 (uint32_t)(g.rows - sr.first) * row_bytes);
+  } else {
+    for (int r = 0; r < g.rows; ++r) {
+      const int y = r < sr.first ? sr.ys + r : r - sr.first;
+      bulk_store(const_cast<char*>(sr.plane) + (int64_t)y * row_bytes, src + (uint32_t)r * row_bytes,
+                 (uint32_t)d.row_copy_bytes);
+    }
+  }
   bulk_commit();
 }
 
+// Bytes that the bulk loads of one tile deliver.
 __device__ __forceinline__ uint32_t tile_bytes_of(const InstDesc& d, const TileGeom& g, int esize) {
-  return 19u * (uint32_t)d.nxp * (uint32_t)esize * (uint32_t)g.rows;
+  const uint32_t row_bytes = (uint32_t)d.nxp * (uint32_t)esize;
+  const uint32_t per_row = (uint32_t)d.row_copy_bytes == row_bytes ? row_bytes : (uint32_t)d.row_copy_bytes;
+  return 19u * per_row * (uint32_t)g.rows;
 }
 
 template <typename T, bool ODD, int MODE>

@@ -236,3 +236,25 @@ def test_subnormal_strain_stays_finite(gpu_lib, kind):
     ref.set_populations(f.astype(np.float32).astype(np.float64))
     ref.step(3)
     assert np.abs(g - ref.populations()).max() <= 1e-24
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("row_align", [256, 4096])
+def test_padded_x_lines(gpu_lib, kind, row_align):
+    """x-lines padded to a larger alignment (the TMA kernel then copies each
+    line's live cells on their own) give the same populations as the oracle."""
+    lbm = gpu_lib
+    nz, ny, nx = 6, 9, 20
+    u = synthetic.random_solenoidal(nx, ny, nz, seed=13)
+    p = lbm.make_params(nx, ny, nz, nu0=0.003, cs=0.13, f0=1e-4, force_mode=lbm.LBM_FORCE_PAPER_SIN,
+                        kernel=kind, row_align=row_align)
+    ref = oracle.OracleLBM(nx, ny, nz, 0.003, 0.13, oracle.FORCE_PAPER_SIN, F0=1e-4)
+    with lbm.Lattice(p) as g:
+        _, nbytes, nxp = lbm.lbm_device_ptr(g.h)
+        assert nxp * 4 % row_align == 0 and nxp >= nx
+        g.init(lbm.LBM_INIT_VELOCITY, u=u)
+        g.step(15)
+        got = g.populations()
+    ref.init_equilibrium(u)
+    ref.step(15)
+    assert full_f_rel_error(got, ref.populations()) <= 1e-5
