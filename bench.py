@@ -474,6 +474,57 @@ def sweep(lbm, device, stream, sizes=(128, 256, 512, 1024), steps=500, warmup=5,
     return {"rows": rows, f"spectral_error_vs_fp64_oracle_128^3_{err_steps}_steps": errs}
 
 
+def c_sweep(lbm, device, stream, n=128, re=5000.0, cs=(0.0, 0.1, 0.16, 0.25), steps=4000,
+            every=250):
+    """The Smagorinsky-constant sweep of Sec. 3.3 (Fig. c_variation): n^3, Re = 5000,
+    C in {0, 0.1, 0.16, 0.25}, the paper's forcing, from the seeded random field.
+    Reports the spectrum time-averaged over the second half of the run, the
+    high-k pile-up indicator E(n/3)/E(peak), and the ESS exponents zeta_p/zeta_3
+    (slopes of log S_p against log |S_3| over r = 2..16, Sec. 3.4) from the
+    structure functions of the last state."""
+    import torch
+    from oracle import diagnostics as dg  # shell count only
+    dev = torch.device("cuda", device)
+    u = make_velocity(n, dev)
+    kmax = dg.max_shell(n, n, n)
+    out = {}
+    for C in cs:
+        nu0 = U0 * n / re
+        p = lbm.make_params(n, nu0=nu0, cs=C, f0=CF * U0 * U0 / n, force_mode=lbm.LBM_FORCE_PAPER_SIN,
+                            device=device, stream=stream.cuda_stream)
+        row = {"C": C, "nu0": nu0}
+        try:
+            with lbm.Lattice(p) as L:
+                L.init(lbm.LBM_INIT_VELOCITY, u=u)
+                E = np.zeros(kmax + 1)
+                navg = 0
+                while L.time < steps:
+                    L.step(every)
+                    L.sync()
+                    if L.time > steps // 2:
+                        E += L.spectrum(kmax)
+                        navg += 1
+                st = L.stats(what=lbm.LBM_STATS_STRUCTURE)
+            E /= max(1, navg)
+            peak = int(np.argmax(E[1:])) + 1
+            row["E"] = [float(v) for v in E[:n // 2 + 1]]
+            row["pileup_E(n/3)/E(peak)"] = float(E[n // 3] / E[peak])
+            r = np.array(st["r"], dtype=float)
+            Sp = st["Sp"]
+            sel = (r >= 2) & (r <= 16)
+            s3 = np.log(np.abs(Sp[sel, 2]))
+            row["ESS_zeta_p_over_zeta_3"] = {
+                p_: float(np.polyfit(s3, np.log(np.abs(Sp[sel, p_ - 1])), 1)[0]) for p_ in (2, 4, 6)}
+            row["F4_r1"] = float(st["F4"][0])
+            row["theta_mean"] = st["theta_mean"]
+        except lbm.LbmError as exc:
+            if exc.code != lbm.LBM_ERR_UNSTABLE:
+                raise
+            row["unstable"] = True
+        out[f"C={C}"] = row
+    return {"n": n, "Re": re, "steps": steps, "c_sweep": out}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -490,6 +541,8 @@ def main():
     ap.add_argument("--only-step", action="store_true",
                     help="time the step kernel only (no e2e, extras or CPU baseline): profiling runs")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2])
+    ap.add_argument("--c-sweep", action="store_true",
+                    help="Smagorinsky-constant sweep at 128^3, Re = 5000 (Sec. 3.3): spectra and ESS exponents")
     ap.add_argument("--sweep", action="store_true",
                     help="roofline sweep N in {128, 256, 512, 1024}, FP32 and FP16, with spectral error at 128^3")
     ap.add_argument("--precision-study", action="store_true",
@@ -516,6 +569,12 @@ def main():
     import paper_2512_23116_gb300 as lbm
     lbm.load()
 
+    if args.c_sweep:
+        stream = torch.cuda.Stream(device=dev)
+        res = c_sweep(lbm, local, stream)
+        if rank == 0:
+            print(json.dumps(res), flush=True)
+        return 0
     if args.sweep:
         stream = torch.cuda.Stream(device=dev)
         res = sweep(lbm, local, stream)

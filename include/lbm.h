@@ -105,6 +105,10 @@ typedef struct lbm_params {
   int32_t row_align;      /* byte alignment of each x-line (power of two >= 16;
                              0: 16).  Padding costs memory, not bandwidth: only
                              the nx live cells of a line are moved */
+  int32_t strain_mode;    /* 0: the strain of Eq. (yu_strain) with the bare shear
+                             rate s9 = s_nu0 (explicit); 1: with the local rate
+                             s9 = s_nu(|S|) of Eq. (les_viscosity), solved per cell
+                             by three fixed-point iterations (self-consistent) */
 } lbm_params;
 
 /* Domain statistics of one instance at one time (all FP64 sums on the device). */

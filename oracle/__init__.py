@@ -82,6 +82,9 @@ def _load():
         lib.orc_strain_norm.restype = ctypes.c_double
         lib.orc_strain_norm.argtypes = [D]
         lib.orc_collide_one.argtypes = [D, D, ctypes.c_double, ctypes.c_double, ctypes.c_int, D, D]
+        lib.orc_strain_norm_selfconsistent.restype = ctypes.c_double
+        lib.orc_strain_norm_selfconsistent.argtypes = [D, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        lib.orc_set_strain_mode.argtypes = [ctypes.c_void_p, ctypes.c_int]
         lib.orc_tau_e.restype = ctypes.c_double
         lib.orc_tau_e.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
         _lib = lib
@@ -171,6 +174,11 @@ def tau_e(nu0: float, C: float, S_norm: float) -> float:
     return float(_load().orc_tau_e(float(nu0), float(C), float(S_norm)))
 
 
+def strain_norm_selfconsistent(mneq, s1: float, nu0: float, C: float) -> float:
+    """|S| with the local shear rate s_nu(|S|) in Eq. (yu_strain) (fixed point)."""
+    return float(_load().orc_strain_norm_selfconsistent(_dp(_vec(mneq, 19)), float(s1), float(nu0), float(C)))
+
+
 def collide_one(fp, F, nu0: float, C: float, fixed_rate: bool = False):
     """Post-collision f'* (19,) and theta of one cell (Eq. mrt_les_guo)."""
     out = np.zeros(19)
@@ -218,6 +226,10 @@ class OracleLBM:
 
     def set_fixed_rate(self, fixed: bool) -> None:
         self._lib.orc_set_fixed_rate(self._h, 1 if fixed else 0)
+
+    def set_strain_mode(self, mode: int) -> None:
+        """0: explicit (bare s_nu0 in Eq. yu_strain); 1: self-consistent s_nu(|S|)."""
+        self._lib.orc_set_strain_mode(self._h, int(mode))
 
     def init_equilibrium(self, u: np.ndarray, drho: np.ndarray | None = None) -> None:
         """f' = M^-1 m^eq(drho, u) in every cell (initial condition)."""

@@ -231,6 +231,28 @@ double orc_tau_e(double nu0, double C, double S_norm) {
   return 0.5 + 3.0 * (nu0 + nu_t);
 }
 
+double orc_strain_norm_selfconsistent(const double mneq[19], double s1, double nu0, double C) {
+  /* g(x) = |S| evaluated with s9 = 1/(1/2 + 3 (nu0 + C x)); the fixed point
+   * x = g(x) is the root of h(x) = g(x) - x.  g decreases in x, so h is
+   * strictly decreasing: h(0) >= 0 and h(g(0)) <= 0 bracket the root. */
+  double lo = 0.0, hi;
+  {
+    double S[6];
+    orc_strain(mneq, s1, 1.0 / (0.5 + 3.0 * nu0), S);
+    hi = orc_strain_norm(S);
+  }
+  if (!(C > 0.0) || hi == 0.0) return hi;
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    double S[6];
+    orc_strain(mneq, s1, 1.0 / (0.5 + 3.0 * (nu0 + C * mid)), S);
+    if (orc_strain_norm(S) - mid > 0.0) lo = mid;
+    else hi = mid;
+    if (hi - lo <= 1e-17 * hi) break;
+  }
+  return 0.5 * (lo + hi);
+}
+
 /* ---- lattice state ------------------------------------------------------ */
 
 struct orc_lbm {
@@ -239,6 +261,7 @@ struct orc_lbm {
   double body[3];
   int force_mode;
   int fixed_rate;
+  int strain_mode;
   int64_t t;
   int c[19][3];
   double w[19];
@@ -297,6 +320,8 @@ void orc_destroy(orc_lbm* L) {
 }
 
 void orc_set_fixed_rate(orc_lbm* L, int fixed) { L->fixed_rate = fixed; }
+
+void orc_set_strain_mode(orc_lbm* L, int mode) { L->strain_mode = mode; }
 
 int64_t orc_time(const orc_lbm* L) { return L->t; }
 
@@ -388,6 +413,9 @@ static void collide_cell(const orc_lbm* L, const double* fp, const double F[3],
   double snorm = 0.0, tau_e;
   if (L->fixed_rate) {
     tau_e = 1.0 / L->s_nu0;
+  } else if (L->strain_mode == 1) {
+    snorm = orc_strain_norm_selfconsistent(mneq, 1.19, L->nu0, L->C);
+    tau_e = orc_tau_e(L->nu0, L->C, snorm);
   } else {
     double S[6];
     orc_strain(mneq, 1.19, L->s_nu0, S);

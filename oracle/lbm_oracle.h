@@ -32,6 +32,8 @@ enum {
   ORC_FORCE_KOLMOGOROV = 3  /* Fx = F0 sin(2 pi y / ny) only */
 };
 
+typedef struct orc_lbm orc_lbm;
+
 /* ---- the method's building blocks (App. A and B) ----------------------- */
 
 /* D3Q19 velocities and weights in the paper's order (App. B table). */
@@ -60,6 +62,15 @@ double orc_strain_norm(const double S[6]);
  * Delta = dx = 1. */
 double orc_tau_e(double nu0, double C, double S_norm);
 
+/* Self-consistent strain norm: Eq. (yu_strain) with s9 = s_nu(|S|) =
+ * 1/(1/2 + 3 (nu0 + C |S|)) (Eq. les_viscosity) instead of the bare rate,
+ * solved for |S| by bisection to round-off.  Returns |S|. */
+double orc_strain_norm_selfconsistent(const double mneq[19], double s1, double nu0, double C);
+
+/* Strain evaluation of the collision: 0 = explicit, s9 = bare s_nu0 (default
+ * reading); 1 = self-consistent (orc_strain_norm_selfconsistent). */
+void orc_set_strain_mode(orc_lbm* L, int mode);
+
 /* One collision (Eq. mrt_les_guo, moment space) of a single cell, outside any
  * lattice: fp = the 19 pre-collision f', F = the force at the cell; returns the
  * post-collision f'* and, when theta is not NULL, tau_e - 1/2.  fixed_rate = 1
@@ -68,8 +79,6 @@ void orc_collide_one(const double fp[19], const double F[3], double nu0, double 
                      int fixed_rate, double fstar[19], double* theta);
 
 /* ---- lattice state -------------------------------------------------------- */
-
-typedef struct orc_lbm orc_lbm;
 
 /* nu0 > 0: bare viscosity; C >= 0: Smagorinsky constant (linear, Eq. eddy_visc);
  * F0: forcing amplitude for the sinusoidal modes; body: constant force.

@@ -55,7 +55,7 @@ class LbmParams(ctypes.Structure):
         ("hist_max", ctypes.c_double), ("stream", ctypes.c_void_p),
         ("kernel", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
         ("stages", ctypes.c_int32), ("threads", ctypes.c_int32),
-        ("row_align", ctypes.c_int32),
+        ("row_align", ctypes.c_int32), ("strain_mode", ctypes.c_int32),
     ]
 
 
@@ -189,7 +189,7 @@ def _ptr(a: np.ndarray):
 def make_params(nx, ny=None, nz=None, *, precision=LBM_FP32, re=0.0, u0=0.0, nu0=0.0, cs=0.0,
                 cf=0.2, f0=0.0, body_force=(0.0, 0.0, 0.0), force_mode=LBM_FORCE_NONE,
                 stats_every=0, hist_bins=0, hist_max=0.0, device=0, stream=None, kernel=0,
-                tile_rows=0, stages=0, threads=0, row_align=0) -> LbmParams:
+                tile_rows=0, stages=0, threads=0, row_align=0, strain_mode=0) -> LbmParams:
     p = LbmParams()
     p.nx, p.ny, p.nz = nx, nx if ny is None else ny, nx if nz is None else nz
     p.precision = precision
@@ -202,6 +202,7 @@ def make_params(nx, ny=None, nz=None, *, precision=LBM_FP32, re=0.0, u0=0.0, nu0
     p.kernel, p.tile_rows = kernel, tile_rows
     p.stages, p.threads = stages, threads
     p.row_align = row_align
+    p.strain_mode = strain_mode
     return p
 
 

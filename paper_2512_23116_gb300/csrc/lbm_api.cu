@@ -156,6 +156,7 @@ int validate(const lbm_params& p, std::string& why) {
   if (p.hist_bins < 0 || p.hist_bins > (1 << 16)) { why = "hist_bins out of [0, 65536]"; return LBM_ERR_INVALID_ARG; }
   if (p.kernel < 0 || p.kernel > 2) { why = "unknown kernel kind"; return LBM_ERR_INVALID_ARG; }
   if (p.tile_rows < 0) { why = "tile_rows < 0"; return LBM_ERR_INVALID_ARG; }
+  if (p.strain_mode < 0 || p.strain_mode > 1) { why = "strain_mode must be 0 or 1"; return LBM_ERR_INVALID_ARG; }
   if (p.row_align != 0 && (p.row_align < 16 || p.row_align > 65536 || (p.row_align & (p.row_align - 1)))) {
     why = "row_align must be 0 or a power of two in [16, 65536]";
     return LBM_ERR_INVALID_ARG;
@@ -264,6 +265,7 @@ int build_tiles(lbm_t h) {
     d.nu0 = (float)I.nu0;
     d.s_nu0 = (float)I.s_nu0;
     d.C = (float)I.C;
+    d.strain_mode = p.strain_mode;
     d.nx = p.nx;
     d.ny = p.ny;
     d.nz = p.nz;

@@ -91,7 +91,7 @@ struct CellDiag {
 // constant (Delta = dx = 1).
 __device__ __forceinline__ void mrt_collide(float (&f)[19], const float Fx, const float Fy,
                                             const float Fz, const float nu0, const float s_nu0,
-                                            const float C, CellDiag& dg) {
+                                            const float C, CellDiag& dg, const int strain_mode = 0) {
   // ---- m = M f' via pair sums and differences -------------------------------
   float s[9], d[9];
 #pragma unroll
@@ -145,22 +145,44 @@ __device__ __forceinline__ void mrt_collide(float (&f)[19], const float Fx, cons
   const float n14 = m14 - gy * uz;
   const float n15 = m15 - gx * uz;
 
-  // ---- strain (Eq. yu_strain, s1 = 1.19, s9 = s_nu0) and closure -----------
+  // ---- strain (Eq. yu_strain, s1 = 1.19) and closure -------------------------
+  // S_ab = s9 T_ab + Q_ab with Q = -(s1 m1/38) on the diagonal; T is traceless,
+  // so |S|^2 = 2 (s9^2 TT + 3 a1^2) (Eq. strain_norm) with TT = T_ab T_ab.
   const float a1 = (LBM_S1 / 38.f) * n1;
-  const float Sxx = -a1 - 0.5f * s_nu0 * n9;
-  const float Syy = -a1 + 0.25f * s_nu0 * (n9 - 3.f * n11);
-  const float Szz = -a1 + 0.25f * s_nu0 * (n9 + 3.f * n11);
-  const float Sxy = -1.5f * s_nu0 * n13;
-  const float Sxz = -1.5f * s_nu0 * n15;
-  const float Syz = -1.5f * s_nu0 * n14;
-  const float SS = Sxx * Sxx + Syy * Syy + Szz * Szz + 2.f * (Sxy * Sxy + Sxz * Sxz + Syz * Syz);
-  // Eq. (strain_norm).  |S| = SS2 rsqrt(SS2); below 1e-30 (|S| < 1e-15, so
-  // nu_t < 1e-15 for any C <= 1) the strain is taken as zero: the reciprocal
-  // square root of a subnormal is infinite, and 0 x inf would poison theta.
-  const float SS2 = 2.f * SS;
-  const float snorm = SS2 > 1e-30f ? SS2 * rsqrtf(SS2) : 0.f;
-  const float theta = 3.f * (nu0 + C * snorm);  // tau_e - 1/2, Eq. (les_viscosity)
-  const float snu = __fdividef(1.f, 0.5f + theta);
+  const float Txx = -0.5f * n9;
+  const float Tyy = 0.25f * (n9 - 3.f * n11);
+  const float Tzz = 0.25f * (n9 + 3.f * n11);
+  const float TT = Txx * Txx + Tyy * Tyy + Tzz * Tzz + 4.5f * (n13 * n13 + n14 * n14 + n15 * n15);
+  const float Qt = 3.f * a1 * a1;
+  // |S| = SS2 rsqrt(SS2); below 1e-30 (|S| < 1e-15, so nu_t < 1e-15 for any
+  // C <= 1) the strain is taken as zero: the reciprocal square root of a
+  // subnormal is infinite, and 0 x inf would poison theta.
+  float SS2 = 2.f * (s_nu0 * s_nu0 * TT + Qt);  // s9 = bare s_nu0
+  float snorm = SS2 > 1e-30f ? SS2 * rsqrtf(SS2) : 0.f;
+  float theta = 3.f * (nu0 + C * snorm);  // tau_e - 1/2, Eq. (les_viscosity)
+  float snu = __fdividef(1.f, 0.5f + theta);
+  if (strain_mode == 1) {
+    // self-consistent: x = |S| with s9 = s_nu(x) = 1/(b + 3 C x), b = 1/2 + 3 nu0,
+    // solves h(x) = x^2 - 2 TT s_nu(x)^2 - 2 Qt = 0.  Without the energy-mode
+    // part (Qt = 0) this is the quadratic 3 C x^2 + b x = sqrt(2 TT), solved in
+    // its cancellation-free form; two Newton steps then add the Qt part.
+    const float b = 0.5f + 3.f * nu0;
+    const float p2 = 2.f * TT;
+    const float p = p2 > 1e-30f ? p2 * rsqrtf(p2) : 0.f;
+    const float xs = __fdividef(2.f * p, b + sqrtf(b * b + 12.f * C * p));
+    const float x2 = xs * xs + 2.f * Qt;
+    float x = x2 > 1e-30f ? x2 * rsqrtf(x2) : 0.f;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      const float sv = __fdividef(1.f, b + 3.f * C * x);
+      const float h = x * x - p2 * sv * sv - 2.f * Qt;
+      const float dh = 2.f * x + 6.f * C * p2 * sv * sv * sv;
+      if (dh > 1e-30f) x -= __fdividef(h, dh);
+    }
+    snorm = x;
+    theta = 3.f * (nu0 + C * snorm);
+    snu = __fdividef(1.f, 0.5f + theta);
+  }
   const float h = 1.f - 0.5f * snu;
 
   // ---- force moments F_m (Eq. meq_fm) --------------------------------------

@@ -16,6 +16,7 @@ struct InstDesc {
   float nu0;               // bare viscosity
   float s_nu0;             // bare shear rate 1/(1/2 + 3 nu0)
   float C;                 // Smagorinsky constant
+  int32_t strain_mode;     // 0: s9 = bare s_nu0 in the strain; 1: self-consistent s_nu(|S|)
   int32_t nx, ny, nz, nxp; // nxp: x stride (nx rounded up to the row alignment)
   int32_t row_copy_bytes;  // bytes of one x-line a bulk copy moves (nx cells, 16-byte multiple)
   int64_t pop_stride;      // nz * ny * nxp

@@ -76,7 +76,7 @@ k_step_direct(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, in
       const float Fx = d.fx_of_y[y] + d.fconst[0];
       const float Fz = d.fz_of_x[x] + d.fconst[2];
       CellDiag g;
-      mrt_collide(f, Fx, Fy, Fz, nu0, s_nu0, C, g);
+      mrt_collide(f, Fx, Fy, Fz, nu0, s_nu0, C, g, d.strain_mode);
       if (MODE != MODE_DIAG) {
         if (!ODD) {
           const int64_t o = cell_off(x, y, z, ny, nxp);

@@ -359,7 +359,7 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
       const float Fx = d.fx_of_y[g.y0 + r] + d.fconst[0];
       const float Fz = fz_table[x];
       CellDiag cd;
-      mrt_collide(f, Fx, Fy, Fz, nu0, s_nu0, C, cd);
+      mrt_collide(f, Fx, Fy, Fz, nu0, s_nu0, C, cd, d.strain_mode);
 #pragma unroll
       for (int a = 0; a < 19; ++a) {
         const int xd = ODD ? (cx(a) > 0 ? xp : (cx(a) < 0 ? xm : x)) : x;

@@ -258,3 +258,31 @@ def test_padded_x_lines(gpu_lib, kind, row_align):
     ref.init_equilibrium(u)
     ref.step(15)
     assert full_f_rel_error(got, ref.populations()) <= 1e-5
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_selfconsistent_strain_mode(gpu_lib, kind):
+    """strain_mode = 1 (local shear rate in Eq. yu_strain, solved per cell)
+    matches the oracle's bisection solution; it differs from the explicit mode."""
+    lbm = gpu_lib
+    n = 16
+    u = synthetic.random_solenoidal(n, seed=21, urms=0.05)
+    F0 = 2e-5
+    p1 = lbm.make_params(n, nu0=2.15e-4 * 4, cs=0.13, f0=F0, force_mode=lbm.LBM_FORCE_PAPER_SIN,
+                         kernel=kind, strain_mode=1)
+    ref = oracle.OracleLBM(n, n, n, 2.15e-4 * 4, 0.13, oracle.FORCE_PAPER_SIN, F0=F0)
+    ref.set_strain_mode(1)
+    with lbm.Lattice(p1) as g:
+        g.init(lbm.LBM_INIT_VELOCITY, u=u)
+        g.step(25)
+        got = g.populations()
+        th = g.fields()["theta"]
+    ref.init_equilibrium(u)
+    ref.step(25)
+    assert full_f_rel_error(got, ref.populations()) <= 1e-5
+    fr = ref.fields()
+    assert np.abs(th - fr["theta"]).max() <= 1e-5 * fr["theta"].max()
+    expl = oracle.OracleLBM(n, n, n, 2.15e-4 * 4, 0.13, oracle.FORCE_PAPER_SIN, F0=F0)
+    expl.init_equilibrium(u)
+    expl.step(25)
+    assert np.abs(expl.fields()["theta"] - fr["theta"]).max() > 1e-6

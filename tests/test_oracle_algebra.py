@@ -208,3 +208,32 @@ def test_parameter_chain():
     # Eq. bare_viscosity round trip
     s = oracle.bare_shear_rate(0.01)
     assert math.isclose((1.0 / s - 0.5) / 3.0, 0.01, rel_tol=1e-14)
+
+
+def test_selfconsistent_strain_closed_form_pure_shear():
+    """Pure shear (only m13 non-equilibrium): |S| = s_nu |P| with |P| the norm at
+    s9 = 1 and s_nu = 1/(1/2 + 3 nu0 + 3 C |S|), so 3C|S|^2 + (1/2 + 3 nu0)|S| - |P| = 0
+    (the closed form of the BGK-Smagorinsky relaxation time)."""
+    nu0, C = 2.15e-4, 0.13
+    m = np.zeros(19)
+    m[13] = -4e-3
+    P = oracle.strain_norm(oracle.strain(m, 1.19, 1.0))
+    a, b = 3 * C, 0.5 + 3 * nu0
+    exact = (-b + math.sqrt(b * b + 4 * a * P)) / (2 * a)
+    assert math.isclose(oracle.strain_norm_selfconsistent(m, 1.19, nu0, C), exact, rel_tol=1e-13)
+    # C = 0 reduces to the explicit formula with the bare rate
+    S0 = oracle.strain_norm(oracle.strain(m, 1.19, 1.0 / (0.5 + 3 * nu0)))
+    assert math.isclose(oracle.strain_norm_selfconsistent(m, 1.19, nu0, 0.0), S0, rel_tol=1e-15)
+    # with the closure active the local rate is slower, so |S| is smaller
+    assert oracle.strain_norm_selfconsistent(m, 1.19, nu0, C) < S0
+
+
+def test_selfconsistent_strain_is_a_fixed_point():
+    rng = np.random.default_rng(11)
+    for _ in range(5):
+        m = np.zeros(19)
+        m[[1, 9, 11, 13, 14, 15]] = rng.normal(scale=2e-3, size=6)
+        nu0, C = 1e-3, 0.2
+        s = oracle.strain_norm_selfconsistent(m, 1.19, nu0, C)
+        again = oracle.strain_norm(oracle.strain(m, 1.19, 1.0 / (0.5 + 3 * (nu0 + C * s))))
+        assert math.isclose(again, s, rel_tol=1e-13)
