@@ -15,6 +15,13 @@ namespace {
 constexpr int kAuxThreads = 256;
 
 __device__ __forceinline__ void cell_xyz(int64_t c, int nx, int ny, int& x, int& y, int& z) {
+  if (c < (int64_t)0x7fffffff) {  // 32-bit division for lattices below 2^31 cells
+    const uint32_t cu = (uint32_t)c, row = cu / (uint32_t)nx;
+    x = (int)(cu - row * (uint32_t)nx);
+    z = (int)(row / (uint32_t)ny);
+    y = (int)(row - (uint32_t)z * (uint32_t)ny);
+    return;
+  }
   const int64_t row = c / nx;
   x = (int)(c - row * nx);
   z = (int)(row / ny);
@@ -61,10 +68,10 @@ __global__ void k_init(InstDesc d, bool odd, int mode, double amp, const double*
       uy = u[ustride + k];
       uz = u[2 * ustride + k];
     }
-    double f[19];
-    equilibrium_fp64(drho, ux, uy, uz, f);
+    float f[19];
+    equilibrium((float)drho, (float)ux, (float)uy, (float)uz, f);
 #pragma unroll
-    for (int a = 0; a < 19; ++a) fb[canon_index(d, a, odd, x, y, z)] = Storage<T>::pack((float)f[a]);
+    for (int a = 0; a < 19; ++a) fb[canon_index(d, a, odd, x, y, z)] = Storage<T>::pack(f[a]);
   }
 }
 

@@ -252,31 +252,31 @@ __device__ __forceinline__ void mrt_collide(float (&f)[19], const float Fx, cons
   dg.theta = theta;
 }
 
-// Local equilibrium f' = M^-1 m^eq(drho, u) (App. B) in FP64, for
-// initialisation: m^eq has entries in rows 0-9, 11, 13-15 only.
-__device__ __forceinline__ void equilibrium_fp64(double drho, double ux, double uy, double uz,
-                                                 double (&f)[19]) {
-  const double rho = 1.0 + drho;
-  const double uxx = ux * ux, uyy = uy * uy, uzz = uz * uz, uu = uxx + uyy + uzz;
-  const double mu0 = drho / 19.0;
-  const double mu1 = (-11.0 * drho + 19.0 * rho * uu) / 2394.0;
-  const double mu2 = (-475.0 / 63.0) * rho * uu / 252.0;
-  const double mu3 = rho * ux / 10.0, mu5 = rho * uy / 10.0, mu7 = rho * uz / 10.0;
-  const double mu4 = -2.0 * rho * ux / 3.0 / 40.0;
-  const double mu6 = -2.0 * rho * uy / 3.0 / 40.0;
-  const double mu8 = -2.0 * rho * uz / 3.0 / 40.0;
-  const double mu9 = rho * (2.0 * uxx - uyy - uzz) / 36.0;
-  const double mu11 = rho * (uyy - uzz) / 12.0;
-  const double mu13 = rho * ux * uy / 4.0, mu14 = rho * uy * uz / 4.0, mu15 = rho * ux * uz / 4.0;
-  const double ca = mu0 - 11.0 * mu1 - 4.0 * mu2;
-  const double cd = mu0 + 8.0 * mu1 + mu2;
-  const double E0 = ca + 2.0 * mu9;
-  const double E1 = ca - mu9 + mu11;
-  const double E2 = ca - mu9 - mu11;
-  const double Exy = cd + mu9 + mu11, Eyz = cd - 2.0 * mu9, Exz = cd + mu9 - mu11;
-  const double X = mu3 + mu4, Y = mu5 + mu6, Z = mu7 + mu8;
-  const double O0 = mu3 - 4.0 * mu4, O1 = mu5 - 4.0 * mu6, O2 = mu7 - 4.0 * mu8;
-  const double O3 = X + Y, O4 = X - Y, O5 = Y + Z, O6 = Y - Z, O7 = X + Z, O8 = X - Z;
+// Local equilibrium f' = M^-1 m^eq(drho, u) (App. B), for initialisation:
+// m^eq has entries in rows 0-9, 11, 13-15 only.  FP32 arithmetic (the result
+// is rounded to the storage precision anyway; FP64 is slow on this part).
+__device__ __forceinline__ void equilibrium(float drho, float ux, float uy, float uz, float (&f)[19]) {
+  const float rho = 1.f + drho;
+  const float uxx = ux * ux, uyy = uy * uy, uzz = uz * uz, uu = uxx + uyy + uzz;
+  const float mu0 = drho * (1.f / 19.f);
+  const float mu1 = (-11.f * drho + 19.f * rho * uu) * (1.f / 2394.f);
+  const float mu2 = (-475.f / 63.f / 252.f) * rho * uu;
+  const float mu3 = rho * ux * 0.1f, mu5 = rho * uy * 0.1f, mu7 = rho * uz * 0.1f;
+  const float mu4 = (-2.f / 3.f / 40.f) * rho * ux;
+  const float mu6 = (-2.f / 3.f / 40.f) * rho * uy;
+  const float mu8 = (-2.f / 3.f / 40.f) * rho * uz;
+  const float mu9 = rho * (2.f * uxx - uyy - uzz) * (1.f / 36.f);
+  const float mu11 = rho * (uyy - uzz) * (1.f / 12.f);
+  const float mu13 = rho * ux * uy * 0.25f, mu14 = rho * uy * uz * 0.25f, mu15 = rho * ux * uz * 0.25f;
+  const float ca = mu0 - 11.f * mu1 - 4.f * mu2;
+  const float cd = mu0 + 8.f * mu1 + mu2;
+  const float E0 = ca + 2.f * mu9;
+  const float E1 = ca - mu9 + mu11;
+  const float E2 = ca - mu9 - mu11;
+  const float Exy = cd + mu9 + mu11, Eyz = cd - 2.f * mu9, Exz = cd + mu9 - mu11;
+  const float X = mu3 + mu4, Y = mu5 + mu6, Z = mu7 + mu8;
+  const float O0 = mu3 - 4.f * mu4, O1 = mu5 - 4.f * mu6, O2 = mu7 - 4.f * mu8;
+  const float O3 = X + Y, O4 = X - Y, O5 = Y + Z, O6 = Y - Z, O7 = X + Z, O8 = X - Z;
   f[0] = E0 + O0;          f[1] = E0 - O0;
   f[2] = E1 + O1;          f[3] = E1 - O1;
   f[4] = E2 + O2;          f[5] = E2 - O2;
@@ -286,7 +286,7 @@ __device__ __forceinline__ void equilibrium_fp64(double drho, double ux, double 
   f[12] = Eyz - mu14 + O6; f[13] = Eyz - mu14 - O6;
   f[14] = Exz + mu15 + O7; f[15] = Exz + mu15 - O7;
   f[16] = Exz - mu15 + O8; f[17] = Exz - mu15 - O8;
-  f[18] = mu0 - 30.0 * mu1 + 12.0 * mu2;
+  f[18] = mu0 - 30.f * mu1 + 12.f * mu2;
 }
 
 __device__ __forceinline__ int wrap_dec(int i, int n) { return i == 0 ? n - 1 : i - 1; }

@@ -12,14 +12,21 @@
 
 namespace lbm {
 
+// Per-thread accumulation: the few cells a thread updates in one tile are
+// summed in FP32 (`t`), and each tile's sums are added to the FP64 totals
+// (`s`) by fold(); the block and grid reductions are FP64.
 struct Acc {
   double s[kNSum];
+  float t[kNSum];
   float thmin, thmax;
   uint32_t bad, cells;
 
   __device__ __forceinline__ void reset() {
 #pragma unroll
-    for (int k = 0; k < kNSum; ++k) s[k] = 0.0;
+    for (int k = 0; k < kNSum; ++k) {
+      s[k] = 0.0;
+      t[k] = 0.f;
+    }
     thmin = FLT_MAX;
     thmax = -FLT_MAX;
     bad = 0;
@@ -29,31 +36,40 @@ struct Acc {
   // Energy E_k = <u.u>/2, injection <F.u>, dissipation 2 nu <S_ij S_ij> with
   // S_ij S_ij = |S|^2/2 (Eqs. energy_balance, strain_norm), theta = tau_e - 1/2.
   __device__ __forceinline__ void add(const CellDiag& g, float Fx, float Fy, float Fz, float C) {
-    const double rho = 1.0 + (double)g.drho;
-    const double ux = g.ux, uy = g.uy, uz = g.uz;
-    const double sn = g.snorm, th = g.theta;
-    const double ss = sn * sn;
-    s[P_DRHO] += (double)g.drho;
-    s[P_MX] += rho * ux;
-    s[P_MY] += rho * uy;
-    s[P_MZ] += rho * uz;
-    s[P_UU] += ux * ux + uy * uy + uz * uz;
-    s[P_FU] += (double)Fx * ux + (double)Fy * uy + (double)Fz * uz;
-    s[P_SS] += ss;
-    s[P_NUTSS] += (double)C * sn * ss;
-    s[P_TH] += th;
-    s[P_TH2] += th * th;
-    s[P_XX] += ux * ux;
-    s[P_YY] += uy * uy;
-    s[P_ZZ] += uz * uz;
-    s[P_XY] += ux * uy;
-    s[P_XZ] += ux * uz;
-    s[P_YZ] += uy * uz;
+    const float rho = 1.f + g.drho;
+    const float ux = g.ux, uy = g.uy, uz = g.uz;
+    const float sn = g.snorm, th = g.theta;
+    const float ss = sn * sn;
+    t[P_DRHO] += g.drho;
+    t[P_MX] += rho * ux;
+    t[P_MY] += rho * uy;
+    t[P_MZ] += rho * uz;
+    t[P_UU] += ux * ux + uy * uy + uz * uz;
+    t[P_FU] += Fx * ux + Fy * uy + Fz * uz;
+    t[P_SS] += ss;
+    t[P_NUTSS] += C * sn * ss;
+    t[P_TH] += th;
+    t[P_TH2] += th * th;
+    t[P_XX] += ux * ux;
+    t[P_YY] += uy * uy;
+    t[P_ZZ] += uz * uz;
+    t[P_XY] += ux * uy;
+    t[P_XZ] += ux * uz;
+    t[P_YZ] += uy * uz;
     thmin = fminf(thmin, g.theta);
     thmax = fmaxf(thmax, g.theta);
     const float chk = g.drho + g.ux + g.uy + g.uz + g.snorm;
     bad += isfinite(chk) ? 0u : 1u;
     cells += 1u;
+  }
+
+  // Move the FP32 tile sums into the FP64 totals.
+  __device__ __forceinline__ void fold() {
+#pragma unroll
+    for (int k = 0; k < kNSum; ++k) {
+      s[k] += (double)t[k];
+      t[k] = 0.f;
+    }
   }
 };
 
@@ -69,6 +85,7 @@ static __device__ __noinline__ void block_flush(Acc& acc, double* __restrict__ d
                                          int bar_id) {
   __shared__ double red[32][kNP];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  acc.fold();
   double v[kNP];
 #pragma unroll
   for (int k = 0; k < kNSum; ++k) v[k] = acc.s[k];
@@ -130,7 +147,9 @@ __device__ __forceinline__ void diag_write(const DiagOut& o, const CellDiag& g, 
     int b = o.hist_bins;
     const float q = g.theta * o.hist_scale;
     if (q >= 0.f && q < (float)o.hist_bins) b = min((int)q, o.hist_bins - 1);
-    atomicAdd(&shist[b], 1u);
+    // lanes that fall into the same bin add once (theta is often uniform)
+    const unsigned same = __match_any_sync(__activemask(), b);
+    if ((threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&shist[b], (uint32_t)__popc(same));
   }
 }
 

@@ -95,6 +95,7 @@ k_step_direct(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, in
       if (MODE != MODE_STEP) acc.add(g, Fx, Fy, Fz, C);
       if (MODE == MODE_DIAG) diag_write(dout, g, x, y, z, nx, ny, nz, use_hist ? shist : dout.hist);
     }
+    if (MODE != MODE_STEP) acc.fold();
   }
   if (MODE != MODE_STEP) {
     if (cur >= 0)

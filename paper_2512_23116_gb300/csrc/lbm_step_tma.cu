@@ -373,6 +373,7 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
         r += 1;
       }
     }
+    if (MODE == MODE_STEP_STATS) acc.fold();
     // hand the tile back: make this warp's shared-memory writes visible to the
     // TMA engine, then one arrival per warp
     fence_async_smem();
