@@ -79,6 +79,7 @@ struct lbm_s {
   int64_t t = 0;
   // kernel configuration
   int kind = 1, rows_fixed = 0, stages = 0, threads = 256, bps = 1, grid = 1, smem = 0;
+  int slot_bytes = 0;  // TMA shared-memory slot layout (kSlot3, kSlot2) or 0
   int tile_bytes_max = 0;
   // reductions
   double* d_partials = nullptr;
@@ -307,6 +308,7 @@ LaunchArgs base_args(lbm_t h) {
   la.grid = h->grid;
   la.threads = h->threads;
   la.stages = h->stages;
+  la.slot_bytes = h->slot_bytes;
   la.smem_bytes = h->smem;
   la.tile_bytes_max = h->tile_bytes_max;
   la.err = h->d_err;
@@ -669,8 +671,18 @@ int create_impl(const lbm_params* params, int count, lbm_t* out) {
 // ---- autotuner ------------------------------------------------------------------
 
 struct Candidate {
-  int kind, threads, stages, tile_bytes, rows;
+  int kind, threads, stages, tile_bytes, rows, slot_bytes;
 };
+
+// TMA candidate with R x-lines per tile: the compile-time slot layout when
+// the stage count has one and R x-lines of every instance fit a slot
+// (row_stage = 19 x-lines of the widest instance), else the runtime stride.
+Candidate tma_candidate(int64_t row_stage, int R, int stages, int threads, bool slots = true) {
+  const int64_t seg = row_stage / 19 * R;  // bytes of R x-lines of one population
+  if (slots && stages == 3 && seg <= kSlot3) return {2, threads, stages, 19 * kSlot3, R, kSlot3};
+  if (slots && stages == 2 && seg <= kSlot2) return {2, threads, stages, 19 * kSlot2, R, kSlot2};
+  return {2, threads, stages, (int)((row_stage * R + 15) / 16 * 16), R, 0};
+}
 
 int apply_candidate(lbm_t h, const Candidate& c) {
   h->kind = c.kind;
@@ -678,12 +690,13 @@ int apply_candidate(lbm_t h, const Candidate& c) {
   h->stages = c.stages;
   h->tile_bytes_max = c.tile_bytes;
   h->rows_fixed = c.rows;
+  h->slot_bytes = c.kind == 2 ? c.slot_bytes : 0;
   if (c.kind == 2) {
     int max_nx = 1;
     for (const Inst& I : h->inst) max_nx = std::max(max_nx, I.p.nx);
     h->smem = tma_smem_bytes(c.stages, c.tile_bytes, max_nx);
     if (tma_prepare(h->precision, h->smem) != cudaSuccess) return LBM_ERR_UNSUPPORTED;
-    h->bps = tma_max_blocks_per_sm(h->precision, c.threads, h->smem);
+    h->bps = tma_max_blocks_per_sm(h->precision, h->slot_bytes, c.threads, h->smem);
   } else {
     h->smem = 0;
     h->bps = direct_max_blocks_per_sm(h->precision, c.threads);
@@ -747,15 +760,16 @@ int choose_config(lbm_t h, const lbm_params& p0) {
   };
   // a fully specified configuration skips the autotuner
   if (requested_kind == 1 && requested_rows > 0 && p0.threads > 0)
-    return apply_candidate(h, {1, p0.threads, 0, 0, requested_rows});
+    return apply_candidate(h, {1, p0.threads, 0, 0, requested_rows, 0});
   if (requested_kind == 2 && requested_rows > 0 && p0.threads > 0 && p0.stages > 0) {
-    const int64_t tb = (row_stage * requested_rows + 15) / 16 * 16;
-    if (!tma_ok || !fits(p0.stages, tb))
+    Candidate c = tma_candidate(row_stage, requested_rows, p0.stages, p0.threads);
+    if (!fits(p0.stages, c.tile_bytes)) c = tma_candidate(row_stage, requested_rows, p0.stages, p0.threads, false);
+    if (!tma_ok || !fits(p0.stages, c.tile_bytes))
       return fail(h, LBM_ERR_UNSUPPORTED, "requested TMA stages do not fit shared memory");
-    return apply_candidate(h, {2, p0.threads, p0.stages, (int)tb, requested_rows});
+    return apply_candidate(h, c);
   }
   if (requested_kind == 1 || requested_kind == 0)
-    cands.push_back({1, 256, 0, 0, requested_rows});
+    cands.push_back({1, 256, 0, 0, requested_rows, 0});
   if ((requested_kind == 2 || requested_kind == 0) && tma_ok) {
     // a stage holds R x-lines of every population (exact multiples of one row stage)
     const int row_opts[] = {1, 2, 3, 4, 6, 8, 12, 16};
@@ -764,15 +778,17 @@ int choose_config(lbm_t h, const lbm_params& p0) {
     for (int R : row_opts) {
       if (requested_rows > 0 && R != requested_rows) continue;
       if (R > 1 && R > min_ny) break;
-      const int64_t tb = (row_stage * R + 15) / 16 * 16;
-      if (tb > 96 * 1024) break;
+      if ((row_stage * R + 15) / 16 * 16 > 96 * 1024) break;
       for (int s : stage_opts) {
-        if (!fits(s, tb)) continue;
-        for (int th : thread_opts) cands.push_back({2, th, s, (int)tb, R});
+        for (int th : thread_opts) {
+          Candidate c = tma_candidate(row_stage, R, s, th);
+          if (!fits(s, c.tile_bytes)) c = tma_candidate(row_stage, R, s, th, false);
+          if (fits(s, c.tile_bytes)) cands.push_back(c);
+        }
       }
     }
     if (requested_kind == 2 && cands.empty() && fits(2, (row_stage + 15) / 16 * 16))
-      cands.push_back({2, 256, 2, (int)((row_stage + 15) / 16 * 16), 1});
+      cands.push_back(tma_candidate(row_stage, 1, 2, 256));
   }
   if (cands.empty())
     return fail(h, LBM_ERR_UNSUPPORTED, "no kernel configuration fits this lattice");

@@ -21,6 +21,7 @@ struct LaunchArgs {
   int grid, threads;
   // TMA kernel configuration
   int stages;
+  int slot_bytes;          // shared-memory slot per population segment: kSlot3, kSlot2 or 0 (rows x nxp)
   int smem_bytes;          // dynamic shared memory of the TMA kernel
   int tile_bytes_max;      // bytes of one stage (19 segments)
   uint32_t* err;           // device error word
@@ -31,11 +32,19 @@ struct LaunchArgs {
 cudaError_t launch_step_direct(const LaunchArgs& la, cudaStream_t st);
 int direct_max_blocks_per_sm(int precision, int threads);
 
+// Compile-time shared-memory slots of the TMA kernel's population segments:
+// 19 slots per stage, three stages of kSlot3 or two of kSlot2 bytes fill the
+// 220 KB dynamic shared-memory budget (with the Fz table of x-lines up to 1440
+// values).  A tile of R x-lines of nxp values fits a slot when R nxp (value
+// size) <= slot.
+constexpr int kSlot3 = 3840;
+constexpr int kSlot2 = 5760;
+
 cudaError_t launch_step_tma(const LaunchArgs& la, cudaStream_t st);
 // Dynamic shared memory of the TMA kernel: barriers, `stages` tile buffers and
 // the Fz(x) table of the widest instance.
 int tma_smem_bytes(int stages, int tile_bytes, int max_nx);
-int tma_max_blocks_per_sm(int precision, int threads, int smem_bytes);
+int tma_max_blocks_per_sm(int precision, int slot_bytes, int threads, int smem_bytes);
 cudaError_t tma_prepare(int precision, int smem_bytes);
 
 // Initial condition: f' = equilibrium of (drho, u), written at AA parity `odd`,

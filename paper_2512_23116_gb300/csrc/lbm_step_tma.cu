@@ -7,6 +7,11 @@
 //   odd step:  slot opp(a) of rows y - cy_a of plane z - cz_a (a periodic wrap
 //              in y splits a segment in two; the x wrap is resolved in shared
 //              memory because whole lines are loaded).
+// In shared memory segment a of a stage starts at a x SLOT bytes, SLOT a
+// compile-time slot size (3840 B with three stages, 5760 B with two: 19 slots
+// per stage, the stages fill the 220 KB budget), so each of a cell's 19
+// shared-memory accesses is one base register plus an immediate offset.  Tiles
+// whose rows do not fit a slot use the runtime stride rows x nxp (SLOT = 0).
 // Segment a of the shared-memory tile holds what cell x reads as f_a at
 // position x - [odd] cx_a; the cell writes f*_a into segment opp(a) at position
 // x + [odd] cx_a.  Over the 19 populations the positions a cell writes are the
@@ -67,15 +72,29 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+// One test of the phase; a thread whose phase has not completed is suspended
+// in hardware (no issue slots) until it completes or kSuspendNs pass.
+constexpr uint32_t kSuspendNs = 100000;
+
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
+  if (kSuspendNs == 0) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(kSuspendNs)
+        : "memory");
+  }
   return ok != 0;
 }
 
@@ -121,16 +140,64 @@ struct TileGeom {
   int ii, z, y0, rows;
 };
 
-__device__ __forceinline__ TileGeom tile_geom(const InstDesc* __restrict__ insts, int ninst, int64_t t,
-                                              int hint) {
-  TileGeom g;
-  g.ii = find_instance(insts, ninst, t, hint);
-  const InstDesc& d = insts[g.ii];
-  const int64_t local = t - d.tile_begin;
-  g.z = (int)(local / d.tiles_per_plane);
-  g.y0 = (int)(local - (int64_t)g.z * d.tiles_per_plane) * d.rows;
-  g.rows = min(d.rows, d.ny - g.y0);
-  return g;
+// Walks a block's tiles t0, t0 + stride, ... (tiles are numbered instance by
+// instance, plane by plane, tile row by tile row), keeping the instance and
+// the (plane, tile row) coordinates up to date incrementally: divisions happen
+// only when the walk enters another instance.
+struct TileWalker {
+  int64_t t;       // current global tile
+  int64_t end;     // one past the last tile of instance ii
+  int ii;          // instance of tile t
+  int tpp;         // tiles per plane of instance ii
+  int rows, ny;    // tile rows and y extent of instance ii
+  int z, ty;       // plane and tile row of tile t
+  int sz, sy;      // stride = sz planes + sy tile rows
+};
+
+__device__ __forceinline__ void walker_enter(TileWalker& w, const InstDesc* __restrict__ insts, int ninst,
+                                             int64_t stride) {
+  w.ii = find_instance(insts, ninst, w.t, w.ii);
+  const InstDesc& d = insts[w.ii];
+  w.end = d.tile_end;
+  w.tpp = d.tiles_per_plane;
+  w.rows = d.rows;
+  w.ny = d.ny;
+  const int64_t local = w.t - d.tile_begin;
+  w.z = (int)(local / w.tpp);
+  w.ty = (int)(local - (int64_t)w.z * w.tpp);
+  w.sz = (int)(stride / w.tpp);
+  w.sy = (int)(stride - (int64_t)w.sz * w.tpp);
+}
+
+__device__ __forceinline__ TileWalker walker_start(const InstDesc* __restrict__ insts, int ninst, int64_t t0,
+                                                   int64_t stride) {
+  TileWalker w;
+  w.t = t0;
+  w.ii = 0;
+  walker_enter(w, insts, ninst, stride);
+  return w;
+}
+
+// Step to the next tile of the block; true when it lies in another instance.
+__device__ __forceinline__ bool walker_next(TileWalker& w, const InstDesc* __restrict__ insts, int ninst,
+                                            int64_t stride, int64_t tile_hi) {
+  w.t += stride;
+  if (w.t >= w.end) {
+    if (w.t < tile_hi) walker_enter(w, insts, ninst, stride);
+    return true;
+  }
+  w.z += w.sz;
+  w.ty += w.sy;
+  if (w.ty >= w.tpp) {
+    w.ty -= w.tpp;
+    w.z += 1;
+  }
+  return false;
+}
+
+__device__ __forceinline__ TileGeom walker_geom(const TileWalker& w) {
+  const int y0 = w.ty * w.rows;
+  return TileGeom{w.ii, w.z, y0, min(w.rows, w.ny - y0)};
 }
 
 // The global rows of segment j of a tile: `first` rows from row ys, then the
@@ -166,11 +233,11 @@ __device__ __forceinline__ SegRows seg_rows(const InstDesc& d, const TileGeom& g
 // padding a segment is one contiguous run (two when a y wrap splits it); with
 // padded x-lines every line is copied on its own, live cells only.  Lane 0
 // must have posted the tile's expected bytes.
-template <typename T, bool ODD>
+template <typename T, bool ODD, int SLOT>
 __device__ __forceinline__ void load_segment(const InstDesc& d, const TileGeom& g, int j, uint32_t buf,
                                              uint32_t bar) {
   const uint32_t row_bytes = (uint32_t)d.nxp * (uint32_t)sizeof(T);
-  const uint32_t seg_bytes = row_bytes * (uint32_t)g.rows;
+  const uint32_t seg_bytes = SLOT ? (uint32_t)SLOT : row_bytes * (uint32_t)d.rows;
   const SegRows sr = seg_rows<T, ODD>(d, g, j);
   const uint32_t dst = buf + (uint32_t)j * seg_bytes;
   if ((uint32_t)d.row_copy_bytes == row_bytes) {
@@ -187,10 +254,10 @@ __device__ __forceinline__ void load_segment(const InstDesc& d, const TileGeom& 
 
 // Producer lane j < 19: write segment j of a finished tile back to where it was
 // loaded from, as this lane's bulk async-group.
-template <typename T, bool ODD>
+template <typename T, bool ODD, int SLOT>
 __device__ __forceinline__ void store_segment(const InstDesc& d, const TileGeom& g, int j, uint32_t buf) {
   const uint32_t row_bytes = (uint32_t)d.nxp * (uint32_t)sizeof(T);
-  const uint32_t seg_bytes = row_bytes * (uint32_t)g.rows;
+  const uint32_t seg_bytes = SLOT ? (uint32_t)SLOT : row_bytes * (uint32_t)d.rows;
   const SegRows sr = seg_rows<T, ODD>(d, g, j);
   const uint32_t src = buf + (uint32_t)j * seg_bytes;
   if ((uint32_t)d.row_copy_bytes == row_bytes) {
@@ -215,12 +282,60 @@ __device__ __forceinline__ uint32_t tile_bytes_of(const InstDesc& d, const TileG
   return 19u * per_row * (uint32_t)g.rows;
 }
 
-template <typename T, bool ODD, int MODE>
+// Per-instance constants of a consumer thread's cell loop.
+struct CellLoop {
+  int nx, nxp;
+  int seg;               // population stride in shared memory (values)
+  int dr, dx;            // a pass of nct cells advances dr rows and dx cells
+  int r0, x0;            // the thread's first cell of a tile
+  float fx_const;        // uniform part of Fx
+  float nu0, s_nu0, C;
+};
+
+// Consumer thread of nct: collide cells r0 nx + x0, + nct, ... of a tile of
+// ncell cells in place in shared memory (the AA read and write positions
+// coincide, see the file comment).  fx: Fx(y) from the tile's first row; SMODE:
+// the strain evaluation (lbm_params.strain_mode).
+template <typename T, bool ODD, int MODE, int SMODE>
+__device__ __forceinline__ void collide_tile(const CellLoop& cl, int ncell, const float* __restrict__ fx,
+                                             const float Fy, T* __restrict__ sbuf,
+                                             const float* __restrict__ fz_table, int nct, Acc& acc) {
+  using S = Storage<T>;
+  const int nx = cl.nx, seg = cl.seg;
+  int r = cl.r0, x = cl.x0;
+  for (int c = r * nx + x; c < ncell; c += nct) {
+    const int xm = wrap_dec(x, nx), xp = wrap_inc(x, nx);
+    T* row = sbuf + r * cl.nxp;
+    float f[19];
+#pragma unroll
+    for (int a = 0; a < 19; ++a) {
+      const int xs = ODD ? (cx(a) > 0 ? xm : (cx(a) < 0 ? xp : x)) : x;
+      f[a] = S::cvt(row[a * seg + xs]);
+    }
+    const float Fx = __ldg(fx + r) + cl.fx_const;
+    const float Fz = fz_table[x];
+    CellDiag cd;
+    mrt_collide(f, Fx, Fy, Fz, cl.nu0, cl.s_nu0, cl.C, cd, SMODE);
+#pragma unroll
+    for (int a = 0; a < 19; ++a) {
+      const int xd = ODD ? (cx(a) > 0 ? xp : (cx(a) < 0 ? xm : x)) : x;
+      row[opp(a) * seg + xd] = S::pack(f[a]);
+    }
+    if (MODE == MODE_STEP_STATS) acc.add(cd, Fx, Fy, Fz, cl.C);
+    x += cl.dx;
+    r += cl.dr;
+    if (x >= nx) {
+      x -= nx;
+      r += 1;
+    }
+  }
+}
+
+template <typename T, bool ODD, int MODE, int SLOT>
 __global__ void __launch_bounds__(512, 1)
 k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64_t tile_hi,
            StatsArgs sa, int stages, int tile_bytes, uint32_t* __restrict__ err, long long wait_ns,
            int withhold_first_load) {
-  using S = Storage<T>;
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nconsumer_warps = (blockDim.x >> 5) - 1;
@@ -252,23 +367,27 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
     // arrival, so that its consumers' bounded wait runs out
     const bool withheld = withhold_first_load && blockIdx.x == 0;
     int loaded = 0;  // tiles whose loads were issued
-    int hint_load = 0, hint_store = 0;
+    if (ntiles == 0) return;
+    TileWalker wl = walker_start(insts, ninst, first, stride);  // next tile to load
+    TileWalker ws = wl;                                         // next tile to store
     for (; loaded < ntiles && loaded < stages; ++loaded) {
-      if (withheld && loaded == 0) continue;
-      const TileGeom g = tile_geom(insts, ninst, first + loaded * stride, hint_load);
-      hint_load = g.ii;
-      const InstDesc& d = insts[g.ii];
-      const uint32_t bar = bar_full + 8u * loaded;
-      if (lane == 0) mbar_expect_tx(bar, tile_bytes_of(d, g, (int)sizeof(T)));
-      __syncwarp();
-      if (seg_lane) load_segment<T, ODD>(d, g, lane, buf0 + (uint32_t)loaded * tile_bytes, bar);
+      if (!(withheld && loaded == 0)) {
+        const TileGeom g = walker_geom(wl);
+        const InstDesc& d = insts[g.ii];
+        const uint32_t bar = bar_full + 8u * loaded;
+        if (lane == 0) mbar_expect_tx(bar, tile_bytes_of(d, g, (int)sizeof(T)));
+        __syncwarp();
+        if (seg_lane) load_segment<T, ODD, SLOT>(d, g, lane, buf0 + (uint32_t)loaded * tile_bytes, bar);
+      }
+      walker_next(wl, insts, ninst, stride, tile_hi);
     }
     int stored = 0;
     bool aborted = false;
+    int s = 0;           // stage of tile `stored`
+    uint32_t phase = 0;  // parity of its barriers' current phase
     for (; stored < ntiles; ++stored) {
-      const int s = stored % stages;
       int done_ok = 1;
-      if (lane == 0) done_ok = mbar_wait(bar_done + 8u * s, (uint32_t)((stored / stages) & 1), wait_ns) ? 1 : 0;
+      if (lane == 0) done_ok = mbar_wait(bar_done + 8u * s, phase, wait_ns) ? 1 : 0;
       done_ok = __shfl_sync(0xffffffffu, done_ok, 0);
       if (!done_ok) {
         if (lane == 0) {
@@ -278,13 +397,13 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
         aborted = true;
         break;
       }
-      const TileGeom g = tile_geom(insts, ninst, first + stored * stride, hint_store);
-      hint_store = g.ii;
+      const TileGeom g = walker_geom(ws);
       const uint32_t buf = buf0 + (uint32_t)s * tile_bytes;
-      if (seg_lane) store_segment<T, ODD>(insts[g.ii], g, lane, buf);
+      if (seg_lane) store_segment<T, ODD, SLOT>(insts[g.ii], g, lane, buf);
+      walker_next(ws, insts, ninst, stride, tile_hi);
       if (loaded < ntiles) {
-        const TileGeom gn = tile_geom(insts, ninst, first + loaded * stride, hint_load);
-        hint_load = gn.ii;
+        const TileGeom gn = walker_geom(wl);
+        walker_next(wl, insts, ninst, stride, tile_hi);
         const InstDesc& dn = insts[gn.ii];
         const uint32_t bar = bar_full + 8u * s;
         if (lane == 0) mbar_expect_tx(bar, tile_bytes_of(dn, gn, (int)sizeof(T)));
@@ -292,9 +411,13 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
         if (seg_lane) {
           // this lane's segment region is free once its own store has read it
           bulk_wait_read_all();
-          load_segment<T, ODD>(dn, gn, lane, buf, bar);
+          load_segment<T, ODD, SLOT>(dn, gn, lane, buf, bar);
         }
         ++loaded;
+      }
+      if (++s == stages) {
+        s = 0;
+        phase ^= 1u;
       }
     }
     if (aborted && lane == 0) {
@@ -310,109 +433,147 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
 
   // ---------------- consumer warps ----------------
   const int ctid = threadIdx.x;
+  const int64_t first = tile_lo + blockIdx.x;
+  const int64_t stride = gridDim.x;
+  if (first >= tile_hi) return;
   Acc acc;
   acc.reset();
   int cur = -1;
   bool ok = true;
-  int k = 0;
-  for (int64_t t = tile_lo + blockIdx.x; t < tile_hi; t += gridDim.x, ++k) {
-    const TileGeom g = tile_geom(insts, ninst, t, cur < 0 ? 0 : cur);
-    const InstDesc& d = insts[g.ii];
-    if (g.ii != cur) {
-      // new instance: flush its predecessor's statistics, reload Fz(x)
+  CellLoop cl{};
+  int smode = 0;
+  const float* fy_of_z = nullptr;
+  float fy_const = 0.f;
+  int s = 0;
+  uint32_t phase = 0;
+  for (TileWalker w = walker_start(insts, ninst, first, stride); w.t < tile_hi;
+       walker_next(w, insts, ninst, stride, tile_hi)) {
+    if (w.ii != cur) {
+      // new instance: flush its predecessor's statistics, reload Fz(x) and the
+      // per-instance constants
       if (MODE == MODE_STEP_STATS && cur >= 0)
         block_flush(acc, sa.partials + ((int64_t)cur * sa.grid + blockIdx.x) * kNP, nct, 1);
       acc.reset();
+      const InstDesc& d = insts[w.ii];
       named_sync(2, nct);
       for (int x = ctid; x < d.nx; x += nct) fz_table[x] = d.fz_of_x[x] + d.fconst[2];
       named_sync(2, nct);
-      cur = g.ii;
+      cur = w.ii;
+      cl.nx = d.nx;
+      cl.nxp = d.nxp;
+      cl.seg = SLOT ? SLOT / (int)sizeof(T) : d.rows * d.nxp;
+      cl.dr = nct / d.nx;
+      cl.dx = nct - cl.dr * d.nx;
+      cl.r0 = ctid / d.nx;
+      cl.x0 = ctid - cl.r0 * d.nx;
+      cl.fx_const = d.fconst[0];
+      cl.nu0 = d.nu0;
+      cl.s_nu0 = d.s_nu0;
+      cl.C = d.C;
+      smode = d.strain_mode;
+      fy_of_z = d.fy_of_z;
+      fy_const = d.fconst[1];
     }
-    const int s = k % stages;
+    const int st = s;
+    const uint32_t ph = phase;
+    if (++s == stages) {
+      s = 0;
+      phase ^= 1u;
+    }
     if (ok) {
       if (*abort_flag) {
         ok = false;
-      } else if (!mbar_wait(bar_full + 8u * s, (uint32_t)((k / stages) & 1), wait_ns)) {
+      } else if (!mbar_wait(bar_full + 8u * st, ph, wait_ns)) {
         atomicOr(err, ERR_TIMEOUT);
         *abort_flag = 1;
         ok = false;
       }
     }
     if (!ok) continue;  // keep the named-barrier schedule of the other consumers
-    const int nx = d.nx, nxp = d.nxp;
-    T* sbuf = reinterpret_cast<T*>(smem + kBarBytes + (size_t)s * tile_bytes);
-    const int seg = g.rows * nxp;
-    const int ncell = g.rows * nx;
-    const float Fy = d.fy_of_z[g.z] + d.fconst[1];
-    const float nu0 = d.nu0, s_nu0 = d.s_nu0, C = d.C;
-    const int dr = nct / nx, dx = nct - dr * nx;
-    int r = ctid / nx, x = ctid - r * nx;
-    for (int c = ctid; c < ncell; c += nct) {
-      const int xm = wrap_dec(x, nx), xp = wrap_inc(x, nx);
-      T* row = sbuf + r * nxp;
-      float f[19];
-#pragma unroll
-      for (int a = 0; a < 19; ++a) {
-        const int xs = ODD ? (cx(a) > 0 ? xm : (cx(a) < 0 ? xp : x)) : x;
-        f[a] = S::cvt(row[a * seg + xs]);
-      }
-      const float Fx = d.fx_of_y[g.y0 + r] + d.fconst[0];
-      const float Fz = fz_table[x];
-      CellDiag cd;
-      mrt_collide(f, Fx, Fy, Fz, nu0, s_nu0, C, cd, d.strain_mode);
-#pragma unroll
-      for (int a = 0; a < 19; ++a) {
-        const int xd = ODD ? (cx(a) > 0 ? xp : (cx(a) < 0 ? xm : x)) : x;
-        row[opp(a) * seg + xd] = S::pack(f[a]);
-      }
-      if (MODE == MODE_STEP_STATS) acc.add(cd, Fx, Fy, Fz, C);
-      x += dx;
-      r += dr;
-      if (x >= nx) {
-        x -= nx;
-        r += 1;
-      }
-    }
+    const TileGeom g = walker_geom(w);
+    const float* fx = insts[w.ii].fx_of_y + g.y0;
+    const float Fy = __ldg(fy_of_z + g.z) + fy_const;
+    const int ncell = g.rows * cl.nx;
+    T* sbuf = reinterpret_cast<T*>(smem + kBarBytes + (size_t)st * tile_bytes);
+    if (smode == 1)
+      collide_tile<T, ODD, MODE, 1>(cl, ncell, fx, Fy, sbuf, fz_table, nct, acc);
+    else
+      collide_tile<T, ODD, MODE, 0>(cl, ncell, fx, Fy, sbuf, fz_table, nct, acc);
     if (MODE == MODE_STEP_STATS) acc.fold();
     // hand the tile back: make this warp's shared-memory writes visible to the
     // TMA engine, then one arrival per warp
     fence_async_smem();
     __syncwarp();
-    if (lane == 0) mbar_arrive(bar_done + 8u * s);
+    if (lane == 0) mbar_arrive(bar_done + 8u * st);
   }
   if (MODE == MODE_STEP_STATS && cur >= 0)
     block_flush(acc, sa.partials + ((int64_t)cur * sa.grid + blockIdx.x) * kNP, nct, 1);
 }
 
-template <typename T, bool ODD, int MODE>
+template <typename T, bool ODD, int MODE, int SLOT>
 cudaError_t launch_tma_t(const LaunchArgs& la, cudaStream_t st) {
   (void)cudaGetLastError();  // errors of earlier calls were reported by their return codes
-  k_step_tma<T, ODD, MODE><<<la.grid, la.threads, la.smem_bytes, st>>>(
+  k_step_tma<T, ODD, MODE, SLOT><<<la.grid, la.threads, la.smem_bytes, st>>>(
       la.insts, la.ninst, la.tile_lo, la.tile_hi, la.sa, la.stages, la.tile_bytes_max, la.err,
       la.wait_ns, la.withhold_first_load);
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t dispatch_tma(const LaunchArgs& la, cudaStream_t st) {
-  if (la.mode == MODE_DIAG) return cudaErrorInvalidValue;
+template <typename T, int SLOT>
+cudaError_t dispatch_tma_s(const LaunchArgs& la, cudaStream_t st) {
   if (la.odd)
-    return la.mode == MODE_STEP ? launch_tma_t<T, true, MODE_STEP>(la, st)
-                                : launch_tma_t<T, true, MODE_STEP_STATS>(la, st);
-  return la.mode == MODE_STEP ? launch_tma_t<T, false, MODE_STEP>(la, st)
-                              : launch_tma_t<T, false, MODE_STEP_STATS>(la, st);
+    return la.mode == MODE_STEP ? launch_tma_t<T, true, MODE_STEP, SLOT>(la, st)
+                                : launch_tma_t<T, true, MODE_STEP_STATS, SLOT>(la, st);
+  return la.mode == MODE_STEP ? launch_tma_t<T, false, MODE_STEP, SLOT>(la, st)
+                              : launch_tma_t<T, false, MODE_STEP_STATS, SLOT>(la, st);
 }
 
 template <typename T>
-cudaError_t set_smem(int smem) {
-  const void* fns[] = {(const void*)k_step_tma<T, false, MODE_STEP>, (const void*)k_step_tma<T, true, MODE_STEP>,
-                       (const void*)k_step_tma<T, false, MODE_STEP_STATS>,
-                       (const void*)k_step_tma<T, true, MODE_STEP_STATS>};
+cudaError_t dispatch_tma(const LaunchArgs& la, cudaStream_t st) {
+  if (la.mode == MODE_DIAG) return cudaErrorInvalidValue;
+  switch (la.slot_bytes) {
+    case 0: return dispatch_tma_s<T, 0>(la, st);
+    case kSlot3: return dispatch_tma_s<T, kSlot3>(la, st);
+    case kSlot2: return dispatch_tma_s<T, kSlot2>(la, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, int SLOT>
+cudaError_t set_smem_s(int smem) {
+  const void* fns[] = {(const void*)k_step_tma<T, false, MODE_STEP, SLOT>,
+                       (const void*)k_step_tma<T, true, MODE_STEP, SLOT>,
+                       (const void*)k_step_tma<T, false, MODE_STEP_STATS, SLOT>,
+                       (const void*)k_step_tma<T, true, MODE_STEP_STATS, SLOT>};
   for (const void* f : fns) {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t set_smem(int smem) {
+  cudaError_t e = set_smem_s<T, 0>(smem);
+  if (e == cudaSuccess) e = set_smem_s<T, kSlot3>(smem);
+  if (e == cudaSuccess) e = set_smem_s<T, kSlot2>(smem);
+  return e;
+}
+
+template <typename T>
+cudaError_t occupancy(int* n, int slot_bytes, int threads, int smem_bytes) {
+  switch (slot_bytes) {
+    case 0:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_step_tma<T, true, MODE_STEP_STATS, 0>, threads,
+                                                           smem_bytes);
+    case kSlot3:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_step_tma<T, true, MODE_STEP_STATS, kSlot3>,
+                                                           threads, smem_bytes);
+    case kSlot2:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_step_tma<T, true, MODE_STEP_STATS, kSlot2>,
+                                                           threads, smem_bytes);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -449,13 +610,13 @@ cudaError_t tma_prepare(int precision, int smem_bytes) {
   return e;
 }
 
-int tma_max_blocks_per_sm(int precision, int threads, int smem_bytes) {
+int tma_max_blocks_per_sm(int precision, int slot_bytes, int threads, int smem_bytes) {
   int n = 0;
   cudaError_t e = cudaErrorInvalidValue;
   switch (precision) {
-    case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_tma<float, true, MODE_STEP_STATS>, threads, smem_bytes); break;
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_tma<__half, true, MODE_STEP_STATS>, threads, smem_bytes); break;
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_tma<__nv_bfloat16, true, MODE_STEP_STATS>, threads, smem_bytes); break;
+    case 0: e = occupancy<float>(&n, slot_bytes, threads, smem_bytes); break;
+    case 1: e = occupancy<__half>(&n, slot_bytes, threads, smem_bytes); break;
+    case 2: e = occupancy<__nv_bfloat16>(&n, slot_bytes, threads, smem_bytes); break;
   }
   return e == cudaSuccess ? n : 0;
 }

@@ -11,7 +11,7 @@ import oracle
 import synthetic
 from oracle import diagnostics as dg
 
-from gpu_helpers import fp32_mass_tolerance, make_pair
+from gpu_helpers import KINDS, fp32_mass_tolerance, make_pair
 
 pytestmark = pytest.mark.gpu
 
@@ -126,9 +126,12 @@ def test_odd_sizes_spectrum_parseval(gpu_lib):
     assert math.isclose(E.sum(), st["E_k"], rel_tol=1e-5)
 
 
-def test_series_records(gpu_lib):
+@pytest.mark.parametrize("kind", KINDS)
+def test_series_records(gpu_lib, kind):
+    """Statistics fused into the step (every 5 steps) match the oracle's fields
+    for every step kernel."""
     lbm = gpu_lib
-    gpu, ref, nu0 = _les_case(lbm, n=16, stats_every=5)
+    gpu, ref, nu0 = _les_case(lbm, n=16, stats_every=5, kind=kind)
     with gpu:
         gpu.step(20)
         recs = gpu.series()
