@@ -53,9 +53,10 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def traffic_per_update(kernel_digest: str):
-    """DRAM bytes per cell update of the step kernel from the committed ncu summary,
-    or None when the kernel source changed since the capture."""
+def traffic_per_update(kernel_digest: str, storage: str = "fp32"):
+    """DRAM bytes per cell update of the step kernel (FP32 or FP16 storage) from
+    the committed ncu summary, or None when the kernel source changed since the
+    capture."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -67,7 +68,7 @@ def traffic_per_update(kernel_digest: str):
                 vals[k.strip()] = v.strip()
     if vals.get("kernel_digest") != kernel_digest:
         return None
-    key = "dram_bytes_per_update_fp32"
+    key = f"dram_bytes_per_update_{storage}"
     return float(vals[key]) if key in vals else None
 
 
@@ -652,6 +653,8 @@ def main():
                 "GB_s": cells * BYTES_PER_UPDATE[prec] * args.steps / (ms2 * 1e-3) / 1e9,
                 "frac_hbm": cells * BYTES_PER_UPDATE[prec] * args.steps / (ms2 * 1e-3) / 1e9 / hbm_peak,
                 "speedup_vs_fp32": ms / ms2, "kernel": cfg2}
+            if prec == 1:
+                extra[f"{n}^3_{name}"]["dram_bytes_per_update"] = traffic_per_update(digest, "fp16")
         del u_dev
         torch.cuda.empty_cache()
         m = args.les_n
