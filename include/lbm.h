@@ -177,10 +177,18 @@ int lbm_count(lbm_t h);
 /* Set instance `inst` to the local equilibrium f' = M^-1 m^eq(drho, u) (App. B)
  * of an initial field (Sec. 3.1).  mode = LBM_INIT_*; amplitude is A of the
  * Taylor-Green modes; for LBM_INIT_VELOCITY, u points to 3 nz ny nx FP64 values
- * ([3][nz][ny][nx]) in host memory (u_on_device = 0; pinned memory copies
- * fastest) or device memory of the handle's device (u_on_device = 1).  Host
- * data are copied in bounded chunks.  Resets the step counter of the handle to
- * 0 when count == 1.  Errors: INVALID_ARG, CUDA. */
+ * ([3][nz][ny][nx]) in
+ *   u_on_device = 0: host memory, copied in bounded chunks through a device
+ *                    staging buffer;
+ *   u_on_device = 1: device memory of the handle's device;
+ *   u_on_device = 2: page-locked host memory (cudaHostAlloc, cudaMallocHost or
+ *                    cudaHostRegister) that the initialisation kernel reads in
+ *                    place over the host link, no staging copy; both ends of
+ *                    the range are checked to be page-locked (INVALID_ARG
+ *                    otherwise) and the whole range must be one such block.
+ * The caller keeps ownership; the call is asynchronous on the handle's stream,
+ * so u must stay valid until the next synchronising call.  Resets the step
+ * counter of the handle to 0 when count == 1.  Errors: INVALID_ARG, CUDA. */
 int lbm_init_field(lbm_t h, int32_t inst, int32_t mode, double amplitude,
                    const double* u, int32_t u_on_device);
 

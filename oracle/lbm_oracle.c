@@ -16,7 +16,7 @@
  *   streaming         push, periodic, two lattices                     Sec. 3.1
  *   forcing           Eqs. (forcing_pattern), (forcing_amplitude)      Sec. 2.2
  *
- * Readings where the paper is silent (stated in the design doc as well):
+ * Readings where the paper is silent:
  *  - populations are stored weight-shifted, f' = f - w, rho0 = 1, so that the
  *    printed m^eq (whose first entry is drho = rho - rho0) is consistent with
  *    M f' (M w = (1, -11, 3, 0, ..., 0));

@@ -228,17 +228,22 @@ def lbm_count(h) -> int:
 
 
 def lbm_init_field(h, inst: int, mode: int, amplitude: float = 0.0, u=None) -> None:
-    """u: None, a host numpy array (3, nz, ny, nx) float64, or a CUDA torch tensor."""
+    """u: None, a host numpy array (3, nz, ny, nx) float64 (staged copies), a
+    page-locked CPU torch tensor (read in place by the kernel: keep it alive
+    until the next synchronising call), or a CUDA torch tensor."""
     lib = load()
     if u is None:
         _check(h, lib.lbm_init_field(h, inst, mode, amplitude, None, 0))
         return
-    if hasattr(u, "is_cuda") and u.is_cuda:
+    if hasattr(u, "is_cuda"):
         import torch
-        if u.dtype != torch.float64 or not u.is_contiguous():
-            raise ValueError("device velocity must be a contiguous float64 tensor")
-        _check(h, lib.lbm_init_field(h, inst, mode, amplitude, ctypes.c_void_p(u.data_ptr()), 1))
-        return
+        where = 1 if u.is_cuda else (2 if u.is_pinned() else None)
+        if where is not None:
+            if u.dtype != torch.float64 or not u.is_contiguous():
+                raise ValueError("velocity tensor must be a contiguous float64 tensor")
+            _check(h, lib.lbm_init_field(h, inst, mode, amplitude, ctypes.c_void_p(u.data_ptr()), where))
+            return
+        u = u.numpy()
     ua = np.ascontiguousarray(u, dtype=np.float64)
     _check(h, lib.lbm_init_field(h, inst, mode, amplitude, ua.ctypes.data_as(ctypes.c_void_p), 0))
 

@@ -232,6 +232,12 @@ void clear_graphs(lbm_t h) {
   h->graphs.clear();
 }
 
+// Blocks of the read-only statistics pass: the direct kernel (256 threads) at
+// full occupancy.
+int diag_grid(lbm_t h) {
+  return h->num_sms * std::max(1, direct_max_blocks_per_sm(h->precision, 256));
+}
+
 // Tile decomposition for the current configuration; uploads the descriptor table.
 int build_tiles(lbm_t h) {
   int64_t tile = 0;
@@ -285,7 +291,9 @@ int build_tiles(lbm_t h) {
   CK(h, cudaMemcpyAsync(h->d_desc, h->h_desc.data(), sizeof(InstDesc) * h->h_desc.size(),
                         cudaMemcpyHostToDevice, h->stream));
   // partials for every block and instance
-  const size_t need = (size_t)h->inst.size() * (size_t)h->grid * kNP;
+  // block partials of a step with statistics (h->grid blocks) or of the
+  // statistics pass (diag_grid blocks)
+  const size_t need = (size_t)h->inst.size() * (size_t)std::max(h->grid, diag_grid(h)) * kNP;
   if (need > h->partials_elems) {
     if (h->d_partials) cudaFree(h->d_partials);
     h->d_partials = nullptr;
@@ -446,12 +454,11 @@ int diag_pass(lbm_t h, int i, bool want_u, bool want_aux, int plane_axis, int pl
   {
     LaunchArgs ld = la;
     ld.threads = 256;
-    const int b = direct_max_blocks_per_sm(h->precision, 256);
-    ld.grid = std::max(1, std::min(h->grid, h->num_sms * std::max(1, b)));
-    ld.sa.grid = h->grid;
+    ld.grid = diag_grid(h);
+    ld.sa.grid = ld.grid;
     CK(h, launch_step_direct(ld, h->stream));
   }
-  CK(h, launch_finish(h->d_partials, (int)h->inst.size(), h->grid, h->d_results, nullptr, nullptr,
+  CK(h, launch_finish(h->d_partials, (int)h->inst.size(), diag_grid(h), h->d_results, nullptr, nullptr,
                       0, h->d_err, h->stream));
   return LBM_OK;
 }
@@ -861,9 +868,24 @@ LBM_API int lbm_init_field(lbm_t h, int32_t inst, int32_t mode, double amplitude
   const bool odd = (h->t & 1) != 0;
   if (mode != LBM_INIT_VELOCITY) {
     CK(h, launch_init(d, h->precision, odd, mode, amplitude, nullptr, 0, 0, I.ncell, h->stream));
-  } else if (u_on_device) {
+  } else if (u_on_device == 1) {
     CK(h, launch_init(d, h->precision, odd, 3, 0.0, u, I.ncell, 0, I.ncell, h->stream));
-  } else {
+  } else if (u_on_device == 2) {
+    // page-locked host memory read in place by the kernel: both ends of the
+    // 3 ncell values must be page-locked memory the device can address
+    const double* ends[2] = {u, u + 3 * I.ncell - 1};
+    const double* dev_u = nullptr;
+    for (int e = 0; e < 2; ++e) {
+      cudaPointerAttributes at{};
+      if (cudaPointerGetAttributes(&at, ends[e]) != cudaSuccess || at.type != cudaMemoryTypeHost ||
+          !at.devicePointer) {
+        (void)cudaGetLastError();
+        return fail(h, LBM_ERR_INVALID_ARG, "u_on_device = 2 needs page-locked host memory");
+      }
+      if (e == 0) dev_u = static_cast<const double*>(at.devicePointer);
+    }
+    CK(h, launch_init(d, h->precision, odd, 3, 0.0, dev_u, I.ncell, 0, I.ncell, h->stream));
+  } else if (u_on_device == 0) {
     const int64_t chunk = std::min<int64_t>(I.ncell, kChunkCells);
     int rc = ensure_scratch(h, sizeof(double) * 3 * (size_t)chunk);
     if (rc != LBM_OK) return rc;
@@ -875,6 +897,8 @@ LBM_API int lbm_init_field(lbm_t h, int32_t inst, int32_t mode, double amplitude
                               cudaMemcpyHostToDevice, h->stream));
       CK(h, launch_init(d, h->precision, odd, 3, 0.0, s, n, c0, n, h->stream));
     }
+  } else {
+    return fail(h, LBM_ERR_INVALID_ARG, "u_on_device must be 0, 1 or 2");
   }
   return LBM_OK;
 }

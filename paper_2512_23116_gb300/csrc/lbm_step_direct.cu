@@ -53,9 +53,9 @@ k_step_direct(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, in
     const int zm = wrap_dec(z, nz), zp = wrap_inc(z, nz);
     const float Fy = d.fy_of_z[z] + d.fconst[1];
     const float nu0 = d.nu0, s_nu0 = d.s_nu0, C = d.C;
+    const int dr = blockDim.x / nx, dx = blockDim.x - dr * nx;  // a pass of blockDim.x cells
+    int r = threadIdx.x / nx, x = threadIdx.x - r * nx;
     for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
-      const int r = c / nx;
-      const int x = c - r * nx;
       const int y = y0 + r;
       const int ym = wrap_dec(y, ny), yp = wrap_inc(y, ny);
       const int xm = wrap_dec(x, nx), xp = wrap_inc(x, nx);
@@ -94,6 +94,12 @@ k_step_direct(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, in
       }
       if (MODE != MODE_STEP) acc.add(g, Fx, Fy, Fz, C);
       if (MODE == MODE_DIAG) diag_write(dout, g, x, y, z, nx, ny, nz, use_hist ? shist : dout.hist);
+      x += dx;
+      r += dr;
+      if (x >= nx) {
+        x -= nx;
+        r += 1;
+      }
     }
     if (MODE != MODE_STEP) acc.fold();
   }

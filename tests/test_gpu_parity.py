@@ -3,7 +3,8 @@
 FP32 storage: relative error of every full population f = f' + w at most
 1e-5 (the per-population tolerance of the 32^3 Taylor-Green case).  FP16 and
 BF16 storage: absolute error of f' at most n_steps x ulp(max |f'|) of the
-storage format (one rounding of the stored value per step)."""
+storage format (one rounding of the stored value per step: the arithmetic is
+FP32 and each step stores its result once in the storage type)."""
 import numpy as np
 import pytest
 
@@ -287,3 +288,33 @@ def test_selfconsistent_strain_mode(gpu_lib, kind):
     expl.init_equilibrium(u)
     expl.step(25)
     assert np.abs(expl.fields()["theta"] - fr["theta"]).max() > 1e-6
+
+
+def test_initial_field_sources_agree(gpu_lib):
+    """lbm_init_field from staged host memory (u_on_device = 0), device memory
+    (1) and page-locked host memory read in place (2) gives identical
+    populations; mode 2 rejects memory that is not page-locked."""
+    import ctypes
+
+    import torch
+
+    lbm = gpu_lib
+    n = 24
+    u = synthetic.random_solenoidal(n, seed=7, urms=0.05)
+    sources = [u, torch.from_numpy(u).cuda(), torch.from_numpy(u).pin_memory()]
+    pops = []
+    for src in sources:
+        with lbm.Lattice(lbm.make_params(n, nu0=0.002, cs=0.13)) as L:
+            L.init(lbm.LBM_INIT_VELOCITY, u=src)
+            L.step(3)
+            pops.append(L.populations())
+    assert np.array_equal(pops[0], pops[1]) and np.array_equal(pops[0], pops[2])
+    with lbm.Lattice(lbm.make_params(n, nu0=0.002, cs=0.13)) as L:
+        pageable = np.ascontiguousarray(u)
+        rc = lbm.load().lbm_init_field(L.h, 0, lbm.LBM_INIT_VELOCITY, 0.0,
+                                       pageable.ctypes.data_as(ctypes.c_void_p), 2)
+        assert rc == lbm.LBM_ERR_INVALID_ARG
+        rc = lbm.load().lbm_init_field(L.h, 0, lbm.LBM_INIT_VELOCITY, 0.0,
+                                       pageable.ctypes.data_as(ctypes.c_void_p), 3)
+        assert rc == lbm.LBM_ERR_INVALID_ARG
+        L.sync()
