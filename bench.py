@@ -72,11 +72,18 @@ def traffic_per_update(kernel_digest: str, storage: str = "fp32"):
     return float(vals[key]) if key in vals else None
 
 
+# Sources that define the step kernel k_step_tma and what it computes per cell.
+STEP_KERNEL_SOURCES = ("lbm_device.cuh", "lbm_internal.h", "lbm_kernels.h", "lbm_reduce.cuh",
+                       "lbm_step_tma.cu")
+
+
 def kernel_digest() -> str:
+    """Hash of the step kernel's sources: a committed ncu traffic figure is only
+    reported while it matches."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2512_23116_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in STEP_KERNEL_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode())
             h.update(fh.read())
