@@ -77,16 +77,24 @@ STEP_KERNEL_SOURCES = ("lbm_device.cuh", "lbm_internal.h", "lbm_kernels.h", "lbm
                        "lbm_step_tma.cu")
 
 
-def kernel_digest() -> str:
-    """Hash of the step kernel's sources: a committed ncu traffic figure is only
-    reported while it matches."""
+def _code_only(text: str) -> str:
+    """C++ source without comments, blank lines and trailing blanks."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = (re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines())
+    return "\n".join(ln for ln in lines if ln)
+
+
+def kernel_digest(csrc: str = "") -> str:
+    """Hash of the step kernel's code (comments excluded): a committed ncu
+    traffic figure is only reported while it matches."""
     import hashlib
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2512_23116_gb300", "csrc")
+    csrc = csrc or os.path.join(ROOT, "paper_2512_23116_gb300", "csrc")
     for f in STEP_KERNEL_SOURCES:
-        with open(os.path.join(csrc, f), "rb") as fh:
+        with open(os.path.join(csrc, f)) as fh:
             h.update(f.encode())
-            h.update(fh.read())
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -25,12 +25,14 @@
 // cp.async.bulk (the TMA engine; x-lines start on 16-byte boundaries, nxp is
 // padded for that) completing on mbarrier transaction counts, and writes each
 // finished tile back with cp.async.bulk shared->global (its own bulk group, so
-// it reloads its segment as soon as its own store has read it).  Consumers read the 19
-// populations of a cell from shared memory, collide in FP32 registers
-// (lbm_device.cuh) and write the 19 results back in place; global memory is
-// touched by the TMA engine only.  Every mbarrier wait is bounded by the
-// global timer: on expiry the block records ERR_TIMEOUT, stops issuing, waits
-// (bounded) for its loads in flight and for its stores, and returns.
+// it reloads its segment as soon as its own store has read it).  Consumers read
+// the 19 populations of a cell from shared memory, collide in FP32 registers
+// (lbm_device.cuh) and write the 19 results back in place; the populations in
+// global memory are moved by the TMA engine only.  Producer and consumers walk
+// the block's tiles with the same incremental tile walker.  Every mbarrier
+// wait is bounded by the global timer: on expiry the block records
+// ERR_TIMEOUT, stops issuing, waits (bounded) for its loads in flight and for
+// its stores, and returns.
 #include <cuda_runtime.h>
 
 #include "lbm_device.cuh"
