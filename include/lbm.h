@@ -192,6 +192,14 @@ int lbm_count(lbm_t h);
 int lbm_init_field(lbm_t h, int32_t inst, int32_t mode, double amplitude,
                    const double* u, int32_t u_on_device);
 
+/* LBM_INIT_VELOCITY from an FP32 field u[3][nz][ny][nx] (same layout, same
+ * u_on_device values 0 / 1 / 2 and the same checks as lbm_init_field).  The
+ * equilibrium is computed from the FP32 rounding of the velocity in either
+ * entry point, so an FP32 field gives exactly the populations of the FP64
+ * field it was rounded from, with half the bytes to move.  No counterpart in
+ * the paper (an input format).  Errors: INVALID_ARG, CUDA. */
+int lbm_init_velocity_f32(lbm_t h, int32_t inst, const float* u, int32_t u_on_device);
+
 /* Advance every instance by n >= 0 time steps of Eq. (mrt_les_guo): collide in
  * moment space, stream with periodic wrap (AA pattern: one population array,
  * even steps write in place, odd steps to the neighbours).  Asynchronous on the

@@ -34,7 +34,8 @@ LBM_STATS_SPECTRUM, LBM_STATS_STRUCTURE = 1, 2
 LBM_MAX_R = 24
 
 EXPORTED = [
-    "lbm_create", "lbm_create_batch", "lbm_destroy", "lbm_count", "lbm_init_field", "lbm_step",
+    "lbm_create", "lbm_create_batch", "lbm_destroy", "lbm_count", "lbm_init_field",
+    "lbm_init_velocity_f32", "lbm_step",
     "lbm_sync", "lbm_time", "lbm_stats", "lbm_series", "lbm_spectrum", "lbm_histogram",
     "lbm_get_populations", "lbm_set_populations", "lbm_set_time", "lbm_get_fields",
     "lbm_get_theta_slice", "lbm_device_ptr", "lbm_get_params", "lbm_kernel_config",
@@ -136,6 +137,7 @@ def load():
         "lbm_destroy": ([H], ctypes.c_int),
         "lbm_count": ([H], ctypes.c_int),
         "lbm_init_field": ([H, i32, i32, ctypes.c_double, ctypes.c_void_p, i32], ctypes.c_int),
+        "lbm_init_velocity_f32": ([H, i32, ctypes.c_void_p, i32], ctypes.c_int),
         "lbm_step": ([H, i64], ctypes.c_int),
         "lbm_sync": ([H], ctypes.c_int),
         "lbm_time": ([H], i64),
@@ -228,24 +230,36 @@ def lbm_count(h) -> int:
 
 
 def lbm_init_field(h, inst: int, mode: int, amplitude: float = 0.0, u=None) -> None:
-    """u: None, a host numpy array (3, nz, ny, nx) float64 (staged copies), a
+    """u: None, a host numpy array (3, nz, ny, nx) (staged copies), a
     page-locked CPU torch tensor (read in place by the kernel: keep it alive
-    until the next synchronising call), or a CUDA torch tensor."""
+    until the next synchronising call), or a CUDA torch tensor.  float32 data
+    go through lbm_init_velocity_f32 (same populations, half the bytes), any
+    other dtype is taken as float64."""
     lib = load()
     if u is None:
         _check(h, lib.lbm_init_field(h, inst, mode, amplitude, None, 0))
         return
+
+    def call(ptr, where, f32):
+        if f32:
+            if mode != LBM_INIT_VELOCITY:
+                raise ValueError("an FP32 field is only accepted for LBM_INIT_VELOCITY")
+            _check(h, lib.lbm_init_velocity_f32(h, inst, ptr, where))
+        else:
+            _check(h, lib.lbm_init_field(h, inst, mode, amplitude, ptr, where))
+
     if hasattr(u, "is_cuda"):
         import torch
         where = 1 if u.is_cuda else (2 if u.is_pinned() else None)
         if where is not None:
-            if u.dtype != torch.float64 or not u.is_contiguous():
-                raise ValueError("velocity tensor must be a contiguous float64 tensor")
-            _check(h, lib.lbm_init_field(h, inst, mode, amplitude, ctypes.c_void_p(u.data_ptr()), where))
+            if u.dtype not in (torch.float64, torch.float32) or not u.is_contiguous():
+                raise ValueError("velocity tensor must be a contiguous float64 or float32 tensor")
+            call(ctypes.c_void_p(u.data_ptr()), where, u.dtype == torch.float32)
             return
         u = u.numpy()
-    ua = np.ascontiguousarray(u, dtype=np.float64)
-    _check(h, lib.lbm_init_field(h, inst, mode, amplitude, ua.ctypes.data_as(ctypes.c_void_p), 0))
+    f32 = getattr(u, "dtype", None) == np.float32
+    ua = np.ascontiguousarray(u, dtype=np.float32 if f32 else np.float64)
+    call(ua.ctypes.data_as(ctypes.c_void_p), 0, f32)
 
 
 def lbm_step(h, n: int) -> None:

@@ -849,6 +849,73 @@ LBM_API int lbm_count(lbm_t h) { return h ? (int)h->inst.size() : 0; }
       return fail((h), LBM_ERR_INVALID_ARG, "instance %d out of range", (int)(i));    \
   } while (0)
 
+namespace {
+
+// A handle with one instance restarts its clock at an initialisation.
+int reset_time(lbm_t h) {
+  if (h->inst.size() == 1 && h->t != 0) {
+    h->t = 0;
+    h->rec_steps.clear();
+    h->inst[0].rec_read = 0;
+    CK(h, cudaMemsetAsync(h->d_seq, 0, sizeof(unsigned long long), h->stream));
+  }
+  return LBM_OK;
+}
+
+// Equilibrium of a given FP64 or FP32 velocity for cells [c0, c0 + n).
+cudaError_t init_from(const InstDesc& d, int precision, bool odd, const double* u, int64_t ustride,
+                      int64_t c0, int64_t n, cudaStream_t st) {
+  return launch_init(d, precision, odd, 3, 0.0, u, ustride, c0, n, st);
+}
+cudaError_t init_from(const InstDesc& d, int precision, bool odd, const float* u, int64_t ustride,
+                      int64_t c0, int64_t n, cudaStream_t st) {
+  return launch_init(d, precision, odd, u, ustride, c0, n, st);
+}
+
+// Local equilibrium of a given velocity field u[3][nz][ny][nx] of type U (FP64
+// or FP32) in host memory (where = 0, staged copies), device memory (1) or
+// page-locked host memory read in place (2).
+template <typename U>
+int init_velocity(lbm_t h, int32_t inst, const U* u, int32_t where) {
+  Inst& I = h->inst[inst];
+  const InstDesc& d = h->h_desc[inst];
+  const bool odd = (h->t & 1) != 0;
+  if (where == 1) {
+    CK(h, init_from(d, h->precision, odd, u, I.ncell, 0, I.ncell, h->stream));
+  } else if (where == 2) {
+    // both ends of the 3 ncell values must be page-locked memory the device can address
+    const U* ends[2] = {u, u + 3 * I.ncell - 1};
+    const U* dev_u = nullptr;
+    for (int e = 0; e < 2; ++e) {
+      cudaPointerAttributes at{};
+      if (cudaPointerGetAttributes(&at, ends[e]) != cudaSuccess || at.type != cudaMemoryTypeHost ||
+          !at.devicePointer) {
+        (void)cudaGetLastError();
+        return fail(h, LBM_ERR_INVALID_ARG, "u_on_device = 2 needs page-locked host memory");
+      }
+      if (e == 0) dev_u = static_cast<const U*>(at.devicePointer);
+    }
+    CK(h, init_from(d, h->precision, odd, dev_u, I.ncell, 0, I.ncell, h->stream));
+  } else if (where == 0) {
+    const int64_t chunk = std::min<int64_t>(I.ncell, kChunkCells);
+    int rc = ensure_scratch(h, sizeof(U) * 3 * (size_t)chunk);
+    if (rc != LBM_OK) return rc;
+    U* s = static_cast<U*>(h->d_scratch);
+    for (int64_t c0 = 0; c0 < I.ncell; c0 += chunk) {
+      const int64_t n = std::min(chunk, I.ncell - c0);
+      for (int dcomp = 0; dcomp < 3; ++dcomp)
+        CK(h, cudaMemcpyAsync(s + dcomp * n, u + dcomp * I.ncell + c0, sizeof(U) * n,
+                              cudaMemcpyHostToDevice, h->stream));
+      CK(h, init_from(d, h->precision, odd, s, n, c0, n, h->stream));
+    }
+  } else {
+    return fail(h, LBM_ERR_INVALID_ARG, "u_on_device must be 0, 1 or 2");
+  }
+  return LBM_OK;
+}
+
+}  // namespace
+
 LBM_API int lbm_init_field(lbm_t h, int32_t inst, int32_t mode, double amplitude, const double* u,
                            int32_t u_on_device) {
   CHECK_INST(h, inst);
@@ -857,50 +924,25 @@ LBM_API int lbm_init_field(lbm_t h, int32_t inst, int32_t mode, double amplitude
     return fail(h, LBM_ERR_INVALID_ARG, "unknown init mode %d", mode);
   if (mode == LBM_INIT_VELOCITY && !u) return fail(h, LBM_ERR_INVALID_ARG, "velocity pointer is null");
   if (!std::isfinite(amplitude)) return fail(h, LBM_ERR_INVALID_ARG, "non-finite amplitude");
-  if (h->inst.size() == 1 && h->t != 0) {
-    h->t = 0;
-    h->rec_steps.clear();
-    h->inst[0].rec_read = 0;
-    CK(h, cudaMemsetAsync(h->d_seq, 0, sizeof(unsigned long long), h->stream));
-  }
-  Inst& I = h->inst[inst];
-  const InstDesc& d = h->h_desc[inst];
-  const bool odd = (h->t & 1) != 0;
-  if (mode != LBM_INIT_VELOCITY) {
-    CK(h, launch_init(d, h->precision, odd, mode, amplitude, nullptr, 0, 0, I.ncell, h->stream));
-  } else if (u_on_device == 1) {
-    CK(h, launch_init(d, h->precision, odd, 3, 0.0, u, I.ncell, 0, I.ncell, h->stream));
-  } else if (u_on_device == 2) {
-    // page-locked host memory read in place by the kernel: both ends of the
-    // 3 ncell values must be page-locked memory the device can address
-    const double* ends[2] = {u, u + 3 * I.ncell - 1};
-    const double* dev_u = nullptr;
-    for (int e = 0; e < 2; ++e) {
-      cudaPointerAttributes at{};
-      if (cudaPointerGetAttributes(&at, ends[e]) != cudaSuccess || at.type != cudaMemoryTypeHost ||
-          !at.devicePointer) {
-        (void)cudaGetLastError();
-        return fail(h, LBM_ERR_INVALID_ARG, "u_on_device = 2 needs page-locked host memory");
-      }
-      if (e == 0) dev_u = static_cast<const double*>(at.devicePointer);
-    }
-    CK(h, launch_init(d, h->precision, odd, 3, 0.0, dev_u, I.ncell, 0, I.ncell, h->stream));
-  } else if (u_on_device == 0) {
-    const int64_t chunk = std::min<int64_t>(I.ncell, kChunkCells);
-    int rc = ensure_scratch(h, sizeof(double) * 3 * (size_t)chunk);
-    if (rc != LBM_OK) return rc;
-    double* s = static_cast<double*>(h->d_scratch);
-    for (int64_t c0 = 0; c0 < I.ncell; c0 += chunk) {
-      const int64_t n = std::min(chunk, I.ncell - c0);
-      for (int dcomp = 0; dcomp < 3; ++dcomp)
-        CK(h, cudaMemcpyAsync(s + dcomp * n, u + dcomp * I.ncell + c0, sizeof(double) * n,
-                              cudaMemcpyHostToDevice, h->stream));
-      CK(h, launch_init(d, h->precision, odd, 3, 0.0, s, n, c0, n, h->stream));
-    }
-  } else {
+  if (mode == LBM_INIT_VELOCITY && (u_on_device < 0 || u_on_device > 2))
     return fail(h, LBM_ERR_INVALID_ARG, "u_on_device must be 0, 1 or 2");
-  }
+  int rc = reset_time(h);
+  if (rc != LBM_OK) return rc;
+  if (mode == LBM_INIT_VELOCITY) return init_velocity<double>(h, inst, u, u_on_device);
+  const Inst& I = h->inst[inst];
+  CK(h, launch_init(h->h_desc[inst], h->precision, (h->t & 1) != 0, mode, amplitude,
+                    nullptr, 0, 0, I.ncell, h->stream));
   return LBM_OK;
+}
+
+LBM_API int lbm_init_velocity_f32(lbm_t h, int32_t inst, const float* u, int32_t u_on_device) {
+  CHECK_INST(h, inst);
+  DevGuard g(h->device);
+  if (!u) return fail(h, LBM_ERR_INVALID_ARG, "velocity pointer is null");
+  if (u_on_device < 0 || u_on_device > 2) return fail(h, LBM_ERR_INVALID_ARG, "u_on_device must be 0, 1 or 2");
+  int rc = reset_time(h);
+  if (rc != LBM_OK) return rc;
+  return init_velocity<float>(h, inst, u, u_on_device);
 }
 
 LBM_API int lbm_step(lbm_t h, int64_t n) {

@@ -40,8 +40,10 @@ __device__ __forceinline__ int64_t canon_index(const InstDesc& d, int a, bool od
   return opp(a) * d.pop_stride + cell_off(xs, ys, zs, d.ny, d.nxp);
 }
 
-template <typename T>
-__global__ void k_init(InstDesc d, bool odd, int mode, double amp, const double* __restrict__ u,
+// U: type of the given velocity (mode 3), FP64 or FP32; the equilibrium is
+// computed from its FP32 rounding either way.
+template <typename T, typename U>
+__global__ void k_init(InstDesc d, bool odd, int mode, double amp, const U* __restrict__ u,
                        int64_t ustride, int64_t c0, int64_t n) {
   T* fb = static_cast<T*>(d.f);
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
@@ -256,25 +258,36 @@ int grid_for(int64_t n) {
   return (int)b;
 }
 
-template <typename T>
-cudaError_t init_t(const InstDesc& d, bool odd, int mode, double amp, const double* u,
+template <typename T, typename U>
+cudaError_t init_t(const InstDesc& d, bool odd, int mode, double amp, const U* u,
                    int64_t ustride, int64_t c0, int64_t n, cudaStream_t st) {
   (void)cudaGetLastError();
-  k_init<T><<<grid_for(n), kAuxThreads, 0, st>>>(d, odd, mode, amp, u, ustride, c0, n);
+  k_init<T, U><<<grid_for(n), kAuxThreads, 0, st>>>(d, odd, mode, amp, u, ustride, c0, n);
   return cudaGetLastError();
+}
+
+template <typename U>
+cudaError_t launch_init_u(const InstDesc& d, int precision, bool odd, int mode, double amp,
+                          const U* u, int64_t ustride, int64_t c0, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  switch (precision) {
+    case 0: return init_t<float, U>(d, odd, mode, amp, u, ustride, c0, n, st);
+    case 1: return init_t<__half, U>(d, odd, mode, amp, u, ustride, c0, n, st);
+    case 2: return init_t<__nv_bfloat16, U>(d, odd, mode, amp, u, ustride, c0, n, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
 cudaError_t launch_init(const InstDesc& d, int precision, bool odd, int mode, double amp,
                         const double* u, int64_t ustride, int64_t c0, int64_t n, cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  switch (precision) {
-    case 0: return init_t<float>(d, odd, mode, amp, u, ustride, c0, n, st);
-    case 1: return init_t<__half>(d, odd, mode, amp, u, ustride, c0, n, st);
-    case 2: return init_t<__nv_bfloat16>(d, odd, mode, amp, u, ustride, c0, n, st);
-  }
-  return cudaErrorInvalidValue;
+  return launch_init_u<double>(d, precision, odd, mode, amp, u, ustride, c0, n, st);
+}
+
+cudaError_t launch_init(const InstDesc& d, int precision, bool odd, const float* u, int64_t ustride,
+                        int64_t c0, int64_t n, cudaStream_t st) {
+  return launch_init_u<float>(d, precision, odd, 3, 0.0, u, ustride, c0, n, st);
 }
 
 cudaError_t launch_get_pop(const InstDesc& d, int precision, bool odd, int a, double* out,

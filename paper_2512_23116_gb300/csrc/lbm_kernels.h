@@ -54,6 +54,10 @@ cudaError_t tma_prepare(int precision, int smem_bytes);
 cudaError_t launch_init(const InstDesc& d, int precision, bool odd, int mode, double amp,
                         const double* u, int64_t ustride, int64_t c0, int64_t n,
                         cudaStream_t st);
+// The same from an FP32 velocity (mode 3): identical populations for the FP32
+// rounding of an FP64 field.
+cudaError_t launch_init(const InstDesc& d, int precision, bool odd, const float* u, int64_t ustride,
+                        int64_t c0, int64_t n, cudaStream_t st);
 // Canonical population a of cells [c0, c0 + n) -> FP64 out[0..n) (+ w_a when !shifted).
 cudaError_t launch_get_pop(const InstDesc& d, int precision, bool odd, int a, double* out,
                            int shifted, int64_t c0, int64_t n, cudaStream_t st);

@@ -292,8 +292,10 @@ def test_selfconsistent_strain_mode(gpu_lib, kind):
 
 def test_initial_field_sources_agree(gpu_lib):
     """lbm_init_field from staged host memory (u_on_device = 0), device memory
-    (1) and page-locked host memory read in place (2) gives identical
-    populations; mode 2 rejects memory that is not page-locked."""
+    (1) and page-locked host memory read in place (2), and
+    lbm_init_velocity_f32 from the FP32 rounding of the same field in each of
+    the three places, give identical populations; mode 2 rejects memory that is
+    not page-locked."""
     import ctypes
 
     import torch
@@ -301,14 +303,18 @@ def test_initial_field_sources_agree(gpu_lib):
     lbm = gpu_lib
     n = 24
     u = synthetic.random_solenoidal(n, seed=7, urms=0.05)
-    sources = [u, torch.from_numpy(u).cuda(), torch.from_numpy(u).pin_memory()]
+    u32 = u.astype(np.float32)
+    sources = [u, torch.from_numpy(u).cuda(), torch.from_numpy(u).pin_memory(),
+               u32, torch.from_numpy(u32).cuda(), torch.from_numpy(u32).pin_memory()]
     pops = []
     for src in sources:
         with lbm.Lattice(lbm.make_params(n, nu0=0.002, cs=0.13)) as L:
             L.init(lbm.LBM_INIT_VELOCITY, u=src)
             L.step(3)
             pops.append(L.populations())
-    assert np.array_equal(pops[0], pops[1]) and np.array_equal(pops[0], pops[2])
+    # the FP32 sources (lbm_init_velocity_f32) give exactly the FP64 ones' populations
+    for p in pops[1:]:
+        assert np.array_equal(pops[0], p)
     with lbm.Lattice(lbm.make_params(n, nu0=0.002, cs=0.13)) as L:
         pageable = np.ascontiguousarray(u)
         rc = lbm.load().lbm_init_field(L.h, 0, lbm.LBM_INIT_VELOCITY, 0.0,
