@@ -17,7 +17,7 @@ namespace lbm {
 constexpr int kSmemHistBins = 12000;  // (bins + 1) * 4 bytes below 48 KB
 
 template <typename T, bool ODD, int MODE>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 k_step_direct(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64_t tile_hi,
               StatsArgs sa, DiagOut dout) {
   using S = Storage<T>;
