@@ -1,6 +1,6 @@
 """Parity at the benchmark's full size, in the launch configuration bench.py times.
 
-The 800^3 forced-HIT DNS-shape workload (FP32, and FP16-shifted storage) is
+The 800^3 forced-HIT DNS-shape workload (FP32, FP16- and BF16-shifted storage) is
 far beyond what the oracle can run, so sampled cells are checked one by one:
 the population array is read in place through lbm_device_ptr (zero-copy), the
 19 pre-collision populations of each sampled cell are taken from the AA layout,
@@ -36,7 +36,7 @@ def _sample_cells(rng, n, k):
     return rng.integers(0, n, size=(k, 3))  # (x, y, z)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_800_cubed_sampled_cells_match_oracle(gpu_lib, precision):
     import torch
 
@@ -64,8 +64,11 @@ def test_800_cubed_sampled_cells_match_oracle(gpu_lib, precision):
             L.step(2)
             L.sync()
             ptr, nbytes, nxp = lbm.lbm_device_ptr(L.h)
-            typestr = "<f4" if precision == 0 else "<f2"
-            A = torch.as_tensor(_CudaArray(ptr, (19, N, N, nxp), typestr), device=dev)
+            if precision == 2:  # bfloat16: no array-interface type string, view the raw 16-bit words
+                A = torch.as_tensor(_CudaArray(ptr, (19, N, N, nxp), "<i2"), device=dev).view(torch.bfloat16)
+            else:
+                A = torch.as_tensor(_CudaArray(ptr, (19, N, N, nxp), "<f4" if precision == 0 else "<f2"),
+                                    device=dev)
             assert A.numel() * A.element_size() == nbytes
             X = torch.as_tensor(cells[:, 0], device=dev)
             Y = torch.as_tensor(cells[:, 1], device=dev)
@@ -102,8 +105,10 @@ def test_800_cubed_sampled_cells_match_oracle(gpu_lib, precision):
                     rel = np.abs(post_h - want) / (want + w[:, None])
                     assert rel.max() <= 1e-5, (parity, rel.max())
                 else:
-                    # one FP16 rounding of the stored result, on top of FP32 arithmetic
-                    spacing = 2.0 ** (np.floor(np.log2(np.abs(want) + 1e-30)) - 10)
+                    # one FP16 / BF16 rounding of the stored result (10 / 7 mantissa bits),
+                    # on top of FP32 arithmetic
+                    mant = 10 if precision == 1 else 7
+                    spacing = 2.0 ** (np.floor(np.log2(np.abs(want) + 1e-30)) - mant)
                     assert np.all(np.abs(post_h - want) <= spacing + 1e-7), parity
             del A
     finally:
