@@ -308,7 +308,10 @@ def test_initial_field_sources_agree(gpu_lib):
                u32, torch.from_numpy(u32).cuda(), torch.from_numpy(u32).pin_memory()]
     pops = []
     for src in sources:
-        with lbm.Lattice(lbm.make_params(n, nu0=0.002, cs=0.13)) as L:
+        # one fixed kernel configuration: the comparison is bitwise, and two
+        # kernels agree only to rounding
+        p = lbm.make_params(n, nu0=0.002, cs=0.13, kernel=2, tile_rows=4, stages=2, threads=256)
+        with lbm.Lattice(p) as L:
             L.init(lbm.LBM_INIT_VELOCITY, u=src)
             L.step(3)
             pops.append(L.populations())
