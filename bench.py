@@ -250,7 +250,7 @@ def time_steps(lbm, lat, stream, steps, warmup, dist):
 
 
 def run_case(lbm, n, precision, C, nu0, steps, warmup, device, stream, u_dev, dist, clocks=None,
-             config="", shape=None, row_align=0):
+             config="", shape=None, row_align=0, layout=0):
     """Create, initialise from the device velocity, time `steps` steps."""
     kind = rows = stages = threads = 0
     if config:
@@ -258,7 +258,8 @@ def run_case(lbm, n, precision, C, nu0, steps, warmup, device, stream, u_dev, di
     nx, ny, nz = shape if shape else (n, n, n)
     p = lbm.make_params(nx, ny, nz, precision=precision, nu0=nu0, cs=C, f0=CF * U0 * U0 / nx,
                         force_mode=lbm.LBM_FORCE_PAPER_SIN, device=device, stream=stream.cuda_stream,
-                        kernel=kind, tile_rows=rows, stages=stages, threads=threads, row_align=row_align)
+                        kernel=kind, tile_rows=rows, stages=stages, threads=threads, row_align=row_align,
+                        layout=layout)
     lat = lbm.Lattice(p)
     lat.init(lbm.LBM_INIT_VELOCITY, u=u_dev)
     if clocks is not None:
@@ -565,6 +566,8 @@ def main():
                     help="spectral error of FP32/FP16/BF16 storage vs the FP64 oracle (64^3) and vs FP32 (800^3)")
     ap.add_argument("--shape", default="",
                     help="nx,ny,nz of a non-cubic box for --only-step profiling runs")
+    ap.add_argument("--layout", type=int, default=0, choices=[0, 1, 2],
+                    help="population array of an --only-step run: 1 population-major, 2 row-interleaved, 0 autotuned")
     ap.add_argument("--config", default="",
                     help="kind,tile_rows,stages,threads: a fixed kernel configuration (no autotuning)")
     args = ap.parse_args()
@@ -617,7 +620,7 @@ def main():
     lat, ms, cfg, st = run_case(lbm, n, args.precision, args.cs if args.only_step else 0.0, nu0,
                                 args.steps, args.warmup, local,
                                 stream, u_dev, dist, clocks, config=args.config, shape=shape,
-                                row_align=args.row_align)
+                                row_align=args.row_align, layout=args.layout)
     assert math.isfinite(st["E_k"]) and st["cells"] == cells, st
     if args.only_step:
         if rank == 0:

@@ -108,7 +108,15 @@ typedef struct lbm_params {
   int32_t strain_mode;    /* 0: the strain of Eq. (yu_strain) with the bare shear
                              rate s9 = s_nu0 (explicit); 1: with the local rate
                              s9 = s_nu(|S|) of Eq. (les_viscosity), solved per cell
-                             by three fixed-point iterations (self-consistent) */
+                             (closed form of the pure-shear quadratic, then two
+                             Newton steps: self-consistent) */
+  int32_t layout;         /* population array in device memory: 1 population-
+                             major [19][nz][ny][nxp], 2 row-interleaved
+                             [nz][ny][19][nxp] (the 19 x-lines of a cell row are
+                             adjacent: longer contiguous runs for the TMA
+                             kernel); 0: the autotuner picks for the TMA kernel,
+                             population-major otherwise.  Results do not depend
+                             on it. */
 } lbm_params;
 
 /* Domain statistics of one instance at one time (all FP64 sums on the device). */
@@ -273,17 +281,19 @@ int lbm_get_fields(lbm_t h, int32_t inst, double* drho, double* u, double* snorm
 int lbm_get_theta_slice(lbm_t h, int32_t inst, int32_t axis, int32_t index, double* host);
 
 /* Device pointer and size in bytes of the population array of `inst`, for
- * zero-copy inspection (read-only by convention; layout [19][nz][ny][nxp] in
- * the AA order of the current parity). */
+ * zero-copy inspection (read-only by convention; layout [19][nz][ny][nxp] or
+ * [nz][ny][19][nxp] as lbm_kernel_config reports, in the AA order of the
+ * current parity). */
 int lbm_device_ptr(lbm_t h, int32_t inst, void** ptr, size_t* bytes, int32_t* nxp);
 
 /* Effective parameters after derivation: nu0, s_nu0, F0, C of `inst`. */
 int lbm_get_params(lbm_t h, int32_t inst, double* nu0, double* s_nu0, double* f0, double* C);
 
 /* Kernel chosen by the autotuner: kind (1 direct, 2 TMA bulk), tile rows,
- * pipeline stages, threads per block, blocks per SM. */
+ * pipeline stages, threads per block, blocks per SM, population layout (1
+ * population-major, 2 row-interleaved).  Any pointer may be NULL. */
 int lbm_kernel_config(lbm_t h, int32_t* kind, int32_t* tile_rows, int32_t* stages,
-                      int32_t* threads, int32_t* blocks_per_sm);
+                      int32_t* threads, int32_t* blocks_per_sm, int32_t* layout);
 
 /* Test hook for the failure path (no counterpart in the paper): the next
  * TMA-kernel step launch of `h` runs with every device-side wait bounded by

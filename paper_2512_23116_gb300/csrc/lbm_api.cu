@@ -80,6 +80,7 @@ struct lbm_s {
   // kernel configuration
   int kind = 1, rows_fixed = 0, stages = 0, threads = 256, bps = 1, grid = 1, smem = 0;
   int slot_bytes = 0;  // TMA shared-memory slot layout (kSlot3, kSlot2) or 0
+  int layout = 0;      // population array: 0 population-major, 1 row-interleaved
   int tile_bytes_max = 0;
   // reductions
   double* d_partials = nullptr;
@@ -158,6 +159,7 @@ int validate(const lbm_params& p, std::string& why) {
   if (p.kernel < 0 || p.kernel > 2) { why = "unknown kernel kind"; return LBM_ERR_INVALID_ARG; }
   if (p.tile_rows < 0) { why = "tile_rows < 0"; return LBM_ERR_INVALID_ARG; }
   if (p.strain_mode < 0 || p.strain_mode > 1) { why = "strain_mode must be 0 or 1"; return LBM_ERR_INVALID_ARG; }
+  if (p.layout < 0 || p.layout > 2) { why = "layout must be 0, 1 or 2"; return LBM_ERR_INVALID_ARG; }
   if (p.row_align != 0 && (p.row_align < 16 || p.row_align > 65536 || (p.row_align & (p.row_align - 1)))) {
     why = "row_align must be 0 or a power of two in [16, 65536]";
     return LBM_ERR_INVALID_ARG;
@@ -281,7 +283,14 @@ int build_tiles(lbm_t h) {
       const int e16 = elems_per_16b(h->precision);
       d.row_copy_bytes = (p.nx + e16 - 1) / e16 * e16 * (int)h->esize;
     }
-    d.pop_stride = (int64_t)p.nz * p.ny * I.nxp;
+    if (h->layout == 0) {  // [19][nz][ny][nxp]
+      d.slot_stride = (int64_t)p.nz * p.ny * I.nxp;
+      d.row_stride = I.nxp;
+    } else {  // [nz][ny][19][nxp]
+      d.slot_stride = I.nxp;
+      d.row_stride = (int64_t)19 * I.nxp;
+    }
+    d.plane_stride = d.row_stride * p.ny;
     d.rows = R;
     d.tiles_per_plane = tpp;
     d.tile_begin = I.tile_begin;
@@ -679,6 +688,7 @@ int create_impl(const lbm_params* params, int count, lbm_t* out) {
 
 struct Candidate {
   int kind, threads, stages, tile_bytes, rows, slot_bytes;
+  int layout;  // 0 population-major, 1 row-interleaved
 };
 
 // TMA candidate with R x-lines per tile: the compile-time slot layout when
@@ -698,6 +708,7 @@ int apply_candidate(lbm_t h, const Candidate& c) {
   h->tile_bytes_max = c.tile_bytes;
   h->rows_fixed = c.rows;
   h->slot_bytes = c.kind == 2 ? c.slot_bytes : 0;
+  h->layout = c.layout;
   if (c.kind == 2) {
     int max_nx = 1;
     for (const Inst& I : h->inst) max_nx = std::max(max_nx, I.p.nx);
@@ -765,18 +776,24 @@ int choose_config(lbm_t h, const lbm_params& p0) {
   auto fits = [&](int stages, int64_t tb) {
     return (int64_t)tma_smem_bytes(stages, (int)tb, max_nx) <= smem_cap;
   };
+  // population layout: lbm_params.layout 1 / 2 fixes it (population-major /
+  // row-interleaved); 0 lets the autotuner try both for the TMA kernel and
+  // means population-major otherwise
+  const int lay_req = p0.layout;
+  const int lay_fixed = lay_req == 2 ? 1 : 0;
   // a fully specified configuration skips the autotuner
   if (requested_kind == 1 && requested_rows > 0 && p0.threads > 0)
-    return apply_candidate(h, {1, p0.threads, 0, 0, requested_rows, 0});
+    return apply_candidate(h, {1, p0.threads, 0, 0, requested_rows, 0, lay_fixed});
   if (requested_kind == 2 && requested_rows > 0 && p0.threads > 0 && p0.stages > 0) {
     Candidate c = tma_candidate(row_stage, requested_rows, p0.stages, p0.threads);
     if (!fits(p0.stages, c.tile_bytes)) c = tma_candidate(row_stage, requested_rows, p0.stages, p0.threads, false);
     if (!tma_ok || !fits(p0.stages, c.tile_bytes))
       return fail(h, LBM_ERR_UNSUPPORTED, "requested TMA stages do not fit shared memory");
+    c.layout = lay_fixed;
     return apply_candidate(h, c);
   }
   if (requested_kind == 1 || requested_kind == 0)
-    cands.push_back({1, 256, 0, 0, requested_rows, 0});
+    cands.push_back({1, 256, 0, 0, requested_rows, 0, lay_fixed});
   if ((requested_kind == 2 || requested_kind == 0) && tma_ok) {
     // a stage holds R x-lines of every population (exact multiples of one row stage)
     const int row_opts[] = {1, 2, 3, 4, 6, 8, 12, 16};
@@ -790,12 +807,20 @@ int choose_config(lbm_t h, const lbm_params& p0) {
         for (int th : thread_opts) {
           Candidate c = tma_candidate(row_stage, R, s, th);
           if (!fits(s, c.tile_bytes)) c = tma_candidate(row_stage, R, s, th, false);
-          if (fits(s, c.tile_bytes)) cands.push_back(c);
+          if (!fits(s, c.tile_bytes)) continue;
+          for (int lay = 0; lay < 2; ++lay) {
+            if ((lay_req == 1 && lay == 1) || (lay_req == 2 && lay == 0)) continue;
+            c.layout = lay;
+            cands.push_back(c);
+          }
         }
       }
     }
-    if (requested_kind == 2 && cands.empty() && fits(2, (row_stage + 15) / 16 * 16))
-      cands.push_back(tma_candidate(row_stage, 1, 2, 256));
+    if (requested_kind == 2 && cands.empty() && fits(2, (row_stage + 15) / 16 * 16)) {
+      Candidate c = tma_candidate(row_stage, 1, 2, 256);
+      c.layout = lay_fixed;
+      cands.push_back(c);
+    }
   }
   if (cands.empty())
     return fail(h, LBM_ERR_UNSUPPORTED, "no kernel configuration fits this lattice");
@@ -1239,13 +1264,14 @@ LBM_API int lbm_get_params(lbm_t h, int32_t inst, double* nu0, double* s_nu0, do
 }
 
 LBM_API int lbm_kernel_config(lbm_t h, int32_t* kind, int32_t* tile_rows, int32_t* stages,
-                              int32_t* threads, int32_t* blocks_per_sm) {
+                              int32_t* threads, int32_t* blocks_per_sm, int32_t* layout) {
   if (!h) return fail(nullptr, LBM_ERR_INVALID_ARG, "null handle");
   if (kind) *kind = h->kind;
   if (tile_rows) *tile_rows = h->inst.empty() ? 0 : h->inst[0].rows;
   if (stages) *stages = h->stages;
   if (threads) *threads = h->threads;
   if (blocks_per_sm) *blocks_per_sm = h->bps;
+  if (layout) *layout = h->layout == 1 ? 2 : 1;
   return LBM_OK;
 }
 

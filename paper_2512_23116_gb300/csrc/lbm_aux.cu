@@ -32,12 +32,12 @@ __device__ __forceinline__ void cell_xyz(int64_t c, int nx, int ny, int& x, int&
 // even time: slot a of x; odd time: slot opp(a) of x - c_a.
 __device__ __forceinline__ int64_t canon_index(const InstDesc& d, int a, bool odd, int x, int y,
                                                int z) {
-  if (!odd) return a * d.pop_stride + cell_off(x, y, z, d.ny, d.nxp);
+  if (!odd) return pop_off(d, a, x, y, z);
   int xs = x - cx(a), ys = y - cy(a), zs = z - cz(a);
   xs = xs < 0 ? xs + d.nx : (xs >= d.nx ? xs - d.nx : xs);
   ys = ys < 0 ? ys + d.ny : (ys >= d.ny ? ys - d.ny : ys);
   zs = zs < 0 ? zs + d.nz : (zs >= d.nz ? zs - d.nz : zs);
-  return opp(a) * d.pop_stride + cell_off(xs, ys, zs, d.ny, d.nxp);
+  return pop_off(d, opp(a), xs, ys, zs);
 }
 
 // U: type of the given velocity (mode 3), FP64 or FP32; the equilibrium is
@@ -103,7 +103,7 @@ __global__ void k_set_pop(InstDesc d, bool odd, int a, const double* __restrict_
   }
 }
 
-// sa, sb: copies of slots a and opp(a) taken at the old parity.
+// sa, sb: dense [nz][ny][nxp] copies of slots a and opp(a) taken at the old parity.
 template <typename T>
 __global__ void k_relayout(InstDesc d, bool from_odd, int a, const T* __restrict__ sa,
                            const T* __restrict__ sb) {
@@ -321,12 +321,17 @@ cudaError_t launch_set_pop(const InstDesc& d, int precision, bool odd, int a, co
 cudaError_t launch_relayout_pair(const InstDesc& d, int precision, bool from_odd, int a,
                                  void* scratch, cudaStream_t st) {
   const size_t es = precision == 0 ? 4 : 2;
-  const size_t plane = (size_t)d.pop_stride * es;
+  const size_t row = (size_t)d.nxp * es;
+  const size_t rows = (size_t)d.nz * d.ny;
+  const size_t plane = row * rows;
   char* s = static_cast<char*>(scratch);
   const char* base = static_cast<const char*>(d.f);
-  cudaError_t e = cudaMemcpyAsync(s, base + (size_t)a * plane, plane, cudaMemcpyDeviceToDevice, st);
+  // slots a and opp(a), x-line by x-line (row_stride apart in either layout), into dense planes
+  cudaError_t e = cudaMemcpy2DAsync(s, row, base + (size_t)a * d.slot_stride * es, (size_t)d.row_stride * es,
+                                    row, rows, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(s + plane, base + (size_t)opp(a) * plane, plane, cudaMemcpyDeviceToDevice, st);
+  e = cudaMemcpy2DAsync(s + plane, row, base + (size_t)opp(a) * d.slot_stride * es, (size_t)d.row_stride * es,
+                        row, rows, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
   const int g = grid_for((int64_t)d.nx * d.ny * d.nz);
   (void)cudaGetLastError();

@@ -316,9 +316,14 @@ __device__ __forceinline__ void equilibrium(float drho, float ux, float uy, floa
 __device__ __forceinline__ int wrap_dec(int i, int n) { return i == 0 ? n - 1 : i - 1; }
 __device__ __forceinline__ int wrap_inc(int i, int n) { return i == n - 1 ? 0 : i + 1; }
 
-// Position of cell (x, y, z) in one population plane of an instance.
+// Position of cell (x, y, z) in a dense [nz][ny][nxp] array (one population).
 __device__ __forceinline__ int64_t cell_off(int x, int y, int z, int ny, int nxp) {
   return ((int64_t)z * ny + y) * nxp + x;
+}
+
+// Position of population slot a of cell (x, y, z) in an instance's array.
+__device__ __forceinline__ int64_t pop_off(const InstDesc& d, int a, int x, int y, int z) {
+  return a * d.slot_stride + z * d.plane_stride + y * d.row_stride + x;
 }
 
 // Index of the instance owning global tile t (tiles are sorted by instance),

@@ -8,7 +8,8 @@ namespace lbm {
 
 // Per-instance description read by every kernel (device memory table).
 struct InstDesc {
-  void* f;                 // populations, storage type, [19][nz][ny][nxp]
+  void* f;                 // populations, storage type; value (a, x, y, z) at
+                           // a slot_stride + z plane_stride + y row_stride + x
   const float* fx_of_y;    // Fx(y) table [ny]   (Eq. forcing_pattern)
   const float* fy_of_z;    // Fy(z) table [nz]
   const float* fz_of_x;    // Fz(x) table [nx]
@@ -19,7 +20,10 @@ struct InstDesc {
   int32_t strain_mode;     // 0: s9 = bare s_nu0 in the strain; 1: self-consistent s_nu(|S|)
   int32_t nx, ny, nz, nxp; // nxp: x stride (nx rounded up to the row alignment)
   int32_t row_copy_bytes;  // bytes of one x-line a bulk copy moves (nx cells, 16-byte multiple)
-  int64_t pop_stride;      // nz * ny * nxp
+  // Population layout (elements): population-major [19][nz][ny][nxp]
+  // (slot_stride = nz ny nxp, row_stride = nxp) or row-interleaved
+  // [nz][ny][19][nxp] (slot_stride = nxp, row_stride = 19 nxp).
+  int64_t slot_stride, plane_stride, row_stride;
   int32_t rows;            // rows (y lines of nx cells) per tile
   int32_t tiles_per_plane; // ceil(ny / rows)
   int64_t tile_begin;      // first global tile of the instance

@@ -42,8 +42,10 @@ k_step_direct(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, in
       cur = ii;
     }
     const InstDesc& d = insts[ii];
-    const int nx = d.nx, ny = d.ny, nz = d.nz, nxp = d.nxp;
-    const int64_t ps = d.pop_stride;
+    const int nx = d.nx, ny = d.ny, nz = d.nz;
+    const int64_t ps = d.slot_stride, pls = d.plane_stride, rs = d.row_stride;
+    // position of cell (x, y, z) within a population slot
+    auto at = [pls, rs](int x, int y, int z) { return z * pls + y * rs + x; };
     const int64_t local = t - d.tile_begin;
     const int z = (int)(local / d.tiles_per_plane);
     const int y0 = (int)(local - (int64_t)z * d.tiles_per_plane) * d.rows;
@@ -61,7 +63,7 @@ k_step_direct(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, in
       const int xm = wrap_dec(x, nx), xp = wrap_inc(x, nx);
       float f[19];
       if (!ODD) {
-        const int64_t o = cell_off(x, y, z, ny, nxp);
+        const int64_t o = at(x, y, z);
 #pragma unroll
         for (int a = 0; a < 19; ++a) f[a] = S::load(fb + a * ps + o);
       } else {
@@ -70,7 +72,7 @@ k_step_direct(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, in
           const int xs = cx(a) > 0 ? xm : (cx(a) < 0 ? xp : x);
           const int ys = cy(a) > 0 ? ym : (cy(a) < 0 ? yp : y);
           const int zs = cz(a) > 0 ? zm : (cz(a) < 0 ? zp : z);
-          f[a] = S::load(fb + opp(a) * ps + cell_off(xs, ys, zs, ny, nxp));
+          f[a] = S::load(fb + opp(a) * ps + at(xs, ys, zs));
         }
       }
       const float Fx = d.fx_of_y[y] + d.fconst[0];
@@ -79,7 +81,7 @@ k_step_direct(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, in
       mrt_collide(f, Fx, Fy, Fz, nu0, s_nu0, C, g, d.strain_mode);
       if (MODE != MODE_DIAG) {
         if (!ODD) {
-          const int64_t o = cell_off(x, y, z, ny, nxp);
+          const int64_t o = at(x, y, z);
 #pragma unroll
           for (int a = 0; a < 19; ++a) fb[opp(a) * ps + o] = S::pack(f[a]);
         } else {
@@ -88,7 +90,7 @@ k_step_direct(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, in
             const int xd = cx(a) > 0 ? xp : (cx(a) < 0 ? xm : x);
             const int yd = cy(a) > 0 ? yp : (cy(a) < 0 ? ym : y);
             const int zd = cz(a) > 0 ? zp : (cz(a) < 0 ? zm : z);
-            fb[a * ps + cell_off(xd, yd, zd, ny, nxp)] = S::pack(f[a]);
+            fb[a * ps + at(xd, yd, zd)] = S::pack(f[a]);
           }
         }
       }

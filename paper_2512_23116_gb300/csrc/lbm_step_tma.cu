@@ -2,7 +2,8 @@
 //
 // A tile is `rows` consecutive x-lines of one z-plane.  In the AA pattern the
 // locations a tile reads are exactly the locations it writes, and they form
-// 19 contiguous segments of rows x nxp values (one per population slot):
+// 19 segments of rows x-lines (one per population slot; contiguous in the
+// population-major layout, x-line by x-line in the row-interleaved one):
 //   even step: slot a of the tile's own rows;
 //   odd step:  slot opp(a) of rows y - cy_a of plane z - cz_a (a periodic wrap
 //              in y splits a segment in two; the x wrap is resolved in shared
@@ -205,18 +206,19 @@ __device__ __forceinline__ TileGeom walker_geom(const TileWalker& w) {
 // The global rows of segment j of a tile: `first` rows from row ys, then the
 // remaining rows from row 0 of the same plane (periodic wrap in y).
 struct SegRows {
-  const char* plane;  // start of the plane (slot, z) in global memory
+  const char* plane;  // row 0 of the slot's plane z in global memory
+  int64_t step;       // bytes from one y row of the slot to the next
   int ys, first;
 };
 
 template <typename T, bool ODD>
 __device__ __forceinline__ SegRows seg_rows(const InstDesc& d, const TileGeom& g, int j) {
-  const int64_t row_bytes = (int64_t)d.nxp * (int64_t)sizeof(T);
-  const int64_t slot_bytes = d.pop_stride * (int64_t)sizeof(T);
+  const int64_t es = (int64_t)sizeof(T);
   const char* base = static_cast<const char*>(d.f);
   SegRows s;
+  s.step = d.row_stride * es;
   if (!ODD) {
-    s.plane = base + j * slot_bytes + (int64_t)g.z * d.ny * row_bytes;
+    s.plane = base + (j * d.slot_stride + g.z * d.plane_stride) * es;
     s.ys = g.y0;
     s.first = g.rows;
   } else {
@@ -224,17 +226,19 @@ __device__ __forceinline__ SegRows seg_rows(const InstDesc& d, const TileGeom& g
     zs = zs < 0 ? zs + d.nz : (zs >= d.nz ? zs - d.nz : zs);
     int ys = g.y0 - c_seg_cy[j];
     ys = ys < 0 ? ys + d.ny : (ys >= d.ny ? ys - d.ny : ys);
-    s.plane = base + c_seg_opp[j] * slot_bytes + (int64_t)zs * d.ny * row_bytes;
+    s.plane = base + (c_seg_opp[j] * d.slot_stride + zs * d.plane_stride) * es;
     s.ys = ys;
     s.first = min(g.rows, d.ny - ys);
   }
   return s;
 }
 
-// Producer lane j < 19: the bulk load(s) of segment j of a tile.  Without
-// padding a segment is one contiguous run (two when a y wrap splits it); with
-// padded x-lines every line is copied on its own, live cells only.  Lane 0
-// must have posted the tile's expected bytes.
+// Producer lane j < 19: the bulk load(s) of segment j of a tile.  In the
+// population-major layout without padding a segment is one contiguous run (two
+// when a y wrap splits it); otherwise (padded x-lines, or the row-interleaved
+// layout, where the rows of a slot are 19 x-lines apart) every x-line is copied
+// on its own, live cells only.  Lane 0 must have posted the tile's expected
+// bytes.
 template <typename T, bool ODD, int SLOT>
 __device__ __forceinline__ void load_segment(const InstDesc& d, const TileGeom& g, int j, uint32_t buf,
                                              uint32_t bar) {
@@ -242,14 +246,14 @@ __device__ __forceinline__ void load_segment(const InstDesc& d, const TileGeom& 
   const uint32_t seg_bytes = SLOT ? (uint32_t)SLOT : row_bytes * (uint32_t)d.rows;
   const SegRows sr = seg_rows<T, ODD>(d, g, j);
   const uint32_t dst = buf + (uint32_t)j * seg_bytes;
-  if ((uint32_t)d.row_copy_bytes == row_bytes) {
+  if ((uint32_t)d.row_copy_bytes == row_bytes && sr.step == (int64_t)row_bytes) {
     bulk_load(dst, sr.plane + (int64_t)sr.ys * row_bytes, (uint32_t)sr.first * row_bytes, bar);
     if (sr.first < g.rows)
       bulk_load(dst + (uint32_t)sr.first * row_bytes, sr.plane, (uint32_t)(g.rows - sr.first) * row_bytes, bar);
   } else {
     for (int r = 0; r < g.rows; ++r) {
       const int y = r < sr.first ? sr.ys + r : r - sr.first;
-      bulk_load(dst + (uint32_t)r * row_bytes, sr.plane + (int64_t)y * row_bytes, (uint32_t)d.row_copy_bytes, bar);
+      bulk_load(dst + (uint32_t)r * row_bytes, sr.plane + (int64_t)y * sr.step, (uint32_t)d.row_copy_bytes, bar);
     }
   }
 }
@@ -262,7 +266,7 @@ __device__ __forceinline__ void store_segment(const InstDesc& d, const TileGeom&
   const uint32_t seg_bytes = SLOT ? (uint32_t)SLOT : row_bytes * (uint32_t)d.rows;
   const SegRows sr = seg_rows<T, ODD>(d, g, j);
   const uint32_t src = buf + (uint32_t)j * seg_bytes;
-  if ((uint32_t)d.row_copy_bytes == row_bytes) {
+  if ((uint32_t)d.row_copy_bytes == row_bytes && sr.step == (int64_t)row_bytes) {
     bulk_store(const_cast<char*>(sr.plane) + (int64_t)sr.ys * row_bytes, src, (uint32_t)sr.first * row_bytes);
     if (sr.first < g.rows)
       bulk_store(const_cast<char*>(sr.plane), src + (uint32_t)sr.first * row_bytes,
@@ -270,7 +274,7 @@ __device__ __forceinline__ void store_segment(const InstDesc& d, const TileGeom&
   } else {
     for (int r = 0; r < g.rows; ++r) {
       const int y = r < sr.first ? sr.ys + r : r - sr.first;
-      bulk_store(const_cast<char*>(sr.plane) + (int64_t)y * row_bytes, src + (uint32_t)r * row_bytes,
+      bulk_store(const_cast<char*>(sr.plane) + (int64_t)y * sr.step, src + (uint32_t)r * row_bytes,
                  (uint32_t)d.row_copy_bytes);
     }
   }

@@ -7,6 +7,7 @@ import numpy as np
 import oracle
 
 KINDS = [1, 2]  # direct-load kernel, TMA bulk-copy kernel
+LAYOUTS = [1, 2]  # population-major, row-interleaved population array
 
 
 def oracle_force_mode(lbm, mode):
@@ -16,11 +17,11 @@ def oracle_force_mode(lbm, mode):
 
 
 def make_pair(lbm, shape, *, nu0, C, force_mode=0, F0=0.0, body=(0.0, 0.0, 0.0), kind=0,
-              precision=0, stats_every=0, hist_bins=0, hist_max=0.0, tile_rows=0):
+              precision=0, stats_every=0, hist_bins=0, hist_max=0.0, tile_rows=0, layout=0):
     nz, ny, nx = shape
     p = lbm.make_params(nx, ny, nz, precision=precision, nu0=nu0, cs=C, f0=F0, body_force=body,
                         force_mode=force_mode, kernel=kind, stats_every=stats_every,
-                        hist_bins=hist_bins, hist_max=hist_max, tile_rows=tile_rows)
+                        hist_bins=hist_bins, hist_max=hist_max, tile_rows=tile_rows, layout=layout)
     gpu = lbm.Lattice(p)
     ref = oracle.OracleLBM(nx, ny, nz, nu0, C, oracle_force_mode(lbm, force_mode), F0=F0, body=body)
     return gpu, ref

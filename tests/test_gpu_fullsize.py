@@ -24,6 +24,19 @@ N = 800
 U0, CF, RE = 0.043, 0.2, 2.0e4
 
 
+def _populations_view(torch, lbm, L, dev, typestr):
+    """Zero-copy [19][nz][ny][nxp] view of the population array in either
+    layout (row-interleaved [nz][ny][19][nxp] arrays are viewed permuted)."""
+    ptr, nbytes, nxp = lbm.lbm_device_ptr(L.h)
+    shape = (19, N, N, nxp) if L.config()["layout"] == 1 else (N, N, 19, nxp)
+    word = "<i2" if typestr == "bf16" else typestr
+    A = torch.as_tensor(_CudaArray(ptr, shape, word), device=dev)
+    if typestr == "bf16":  # no array-interface type string: view the raw 16-bit words
+        A = A.view(torch.bfloat16)
+    assert A.numel() * A.element_size() == nbytes
+    return A if L.config()["layout"] == 1 else A.permute(2, 0, 1, 3)
+
+
 class _CudaArray:
     """Minimal __cuda_array_interface__ view of library-owned device memory."""
 
@@ -63,13 +76,7 @@ def test_800_cubed_sampled_cells_match_oracle(gpu_lib, precision):
             torch.cuda.empty_cache()
             L.step(2)
             L.sync()
-            ptr, nbytes, nxp = lbm.lbm_device_ptr(L.h)
-            if precision == 2:  # bfloat16: no array-interface type string, view the raw 16-bit words
-                A = torch.as_tensor(_CudaArray(ptr, (19, N, N, nxp), "<i2"), device=dev).view(torch.bfloat16)
-            else:
-                A = torch.as_tensor(_CudaArray(ptr, (19, N, N, nxp), "<f4" if precision == 0 else "<f2"),
-                                    device=dev)
-            assert A.numel() * A.element_size() == nbytes
+            A = _populations_view(torch, lbm, L, dev, ["<f4", "<f2", "bf16"][precision])
             X = torch.as_tensor(cells[:, 0], device=dev)
             Y = torch.as_tensor(cells[:, 1], device=dev)
             Z = torch.as_tensor(cells[:, 2], device=dev)
@@ -133,8 +140,7 @@ def test_800_cubed_mass_conservation(gpu_lib):
             L.init(lbm.LBM_INIT_VELOCITY, u=u)
             del u
             torch.cuda.empty_cache()
-            ptr, nbytes, nxp = lbm.lbm_device_ptr(L.h)
-            A = torch.as_tensor(_CudaArray(ptr, (19, N, N, nxp), "<f4"), device=dev)
+            A = _populations_view(torch, lbm, L, dev, "<f4")
 
             def mass():
                 s = torch.zeros((), dtype=torch.float64, device=dev)

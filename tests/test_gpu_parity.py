@@ -12,21 +12,23 @@ import oracle
 import synthetic
 from oracle import fields
 
-from gpu_helpers import KINDS, fp32_mass_tolerance, full_f_rel_error, make_pair, random_populations, ulp
+from gpu_helpers import KINDS, LAYOUTS, fp32_mass_tolerance, full_f_rel_error, make_pair, random_populations, ulp
 
 pytestmark = pytest.mark.gpu
 
 
+@pytest.mark.parametrize("layout", LAYOUTS)
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("steps", [100, 37])
-def test_tgv3d_32_cubed_constant_force(gpu_lib, kind, steps):
+def test_tgv3d_32_cubed_constant_force(gpu_lib, kind, steps, layout):
     """32^3 Taylor-Green, u0 = 0.05, rho = 1, nu0 = 0.01, C = 0.1, F = 1e-6 x."""
     lbm = gpu_lib
     n, F = 32, (1e-6, 0.0, 0.0)
     gpu, ref = make_pair(lbm, (n, n, n), nu0=0.01, C=0.1, force_mode=lbm.LBM_FORCE_CONST, body=F,
-                         kind=kind)
+                         kind=kind, layout=layout)
     with gpu:
         assert gpu.config()["kind"] == kind
+        assert gpu.config()["layout"] == layout
         gpu.init(lbm.LBM_INIT_TGV3D, amplitude=0.05)
         f0 = gpu.populations()
         gpu.step(steps)
@@ -46,9 +48,10 @@ def test_tgv3d_32_cubed_constant_force(gpu_lib, kind, steps):
     assert np.abs(dj - want).max() <= 1e-3 * np.abs(want).max()
 
 
+@pytest.mark.parametrize("layout", LAYOUTS)
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("shape", [(10, 12, 20), (7, 9, 33), (16, 16, 16)])
-def test_random_les_field_paper_forcing(gpu_lib, kind, shape):
+def test_random_les_field_paper_forcing(gpu_lib, kind, shape, layout):
     """Random solenoidal field (seeded generator), the paper's sinusoidal forcing,
     C = 0.13, LES viscosity; ragged sizes exercise padding and wrap."""
     lbm = gpu_lib
@@ -56,7 +59,7 @@ def test_random_les_field_paper_forcing(gpu_lib, kind, shape):
     u = synthetic.random_solenoidal(nx, ny, nz, seed=7, urms=0.05)
     F0 = oracle.forcing_amplitude(0.2, 0.043, nx) * 50  # larger than the paper's, to be visible
     gpu, ref = make_pair(lbm, shape, nu0=2.15e-4 * 10, C=0.13, force_mode=lbm.LBM_FORCE_PAPER_SIN,
-                         F0=F0, kind=kind)
+                         F0=F0, kind=kind, layout=layout)
     with gpu:
         gpu.init(lbm.LBM_INIT_VELOCITY, u=u)
         gpu.step(51)
@@ -132,15 +135,18 @@ def test_C_zero_is_constant_viscosity(gpu_lib, kind):
     assert full_f_rel_error(g, ref.populations()) <= 1e-5
 
 
+@pytest.mark.parametrize("layout", LAYOUTS)
 @pytest.mark.parametrize("kind", KINDS)
-def test_checkpoint_resume_bitwise(gpu_lib, kind):
+def test_checkpoint_resume_bitwise(gpu_lib, kind, layout):
     """get_populations + set_time + set_populations resumes bit for bit, from an
     odd time (twisted AA layout) into a fresh handle."""
     lbm = gpu_lib
     shape = (8, 10, 12)
     u = synthetic.random_solenoidal(12, 10, 8, seed=9)
-    gpu_a, _ = make_pair(lbm, shape, nu0=0.003, C=0.13, force_mode=lbm.LBM_FORCE_PAPER_SIN, F0=1e-4, kind=kind)
-    gpu_b, _ = make_pair(lbm, shape, nu0=0.003, C=0.13, force_mode=lbm.LBM_FORCE_PAPER_SIN, F0=1e-4, kind=kind)
+    gpu_a, _ = make_pair(lbm, shape, nu0=0.003, C=0.13, force_mode=lbm.LBM_FORCE_PAPER_SIN, F0=1e-4, kind=kind,
+                         layout=layout)
+    gpu_b, _ = make_pair(lbm, shape, nu0=0.003, C=0.13, force_mode=lbm.LBM_FORCE_PAPER_SIN, F0=1e-4, kind=kind,
+                         layout=layout)
     with gpu_a, gpu_b:
         gpu_a.init(lbm.LBM_INIT_VELOCITY, u=u)
         gpu_a.step(13)
@@ -190,8 +196,9 @@ def test_all_kernels_agree(gpu_lib):
         assert np.abs(out[0] - o).max() <= 1e-7
 
 
+@pytest.mark.parametrize("layout", LAYOUTS)
 @pytest.mark.parametrize("kind", KINDS)
-def test_batch_of_uneven_instances(gpu_lib, kind):
+def test_batch_of_uneven_instances(gpu_lib, kind, layout):
     """Three instances of different sizes and physics in one handle (one launch
     per step) match three separate oracle runs."""
     lbm = gpu_lib
@@ -204,7 +211,7 @@ def test_batch_of_uneven_instances(gpu_lib, kind):
     for i, s in enumerate(specs):
         nz, ny, nx = s["shape"]
         params.append(lbm.make_params(nx, ny, nz, nu0=s["nu0"], cs=s["C"], f0=s["F0"], body_force=s["body"],
-                                      force_mode=s["fm"], kernel=kind))
+                                      force_mode=s["fm"], kernel=kind, layout=layout))
         refs.append(oracle.OracleLBM(nx, ny, nz, s["nu0"], s["C"],
                                      {0: 0, 1: 1, 2: 2, 3: 3}[s["fm"]], F0=s["F0"], body=s["body"]))
         inits.append(synthetic.random_solenoidal(nx, ny, nz, seed=20 + i))
@@ -350,3 +357,30 @@ def test_tma_shared_memory_layouts_agree(gpu_lib, precision):
             L.step(33)
             out.append(L.populations())
     assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_population_layouts_agree(gpu_lib, kind):
+    """The population-major and row-interleaved arrays give bitwise-equal
+    canonical populations and statistics (same kernel configuration), through
+    even and odd steps, a statistics step and a parity change."""
+    lbm = gpu_lib
+    nx, ny, nz = 24, 10, 7
+    u = synthetic.random_solenoidal(nx, ny, nz, seed=11)
+    out, st = [], []
+    for layout in (1, 2):
+        cfg = dict(kernel=2, tile_rows=2, stages=2, threads=256) if kind == 2 else dict(kernel=1, tile_rows=1,
+                                                                                       threads=256)
+        p = lbm.make_params(nx, ny, nz, nu0=0.002, cs=0.13, f0=1e-4, force_mode=lbm.LBM_FORCE_PAPER_SIN,
+                            stats_every=4, layout=layout, **cfg)
+        with lbm.Lattice(p) as L:
+            assert L.config()["layout"] == layout
+            L.init(lbm.LBM_INIT_VELOCITY, u=u)
+            L.step(9)
+            lbm.lbm_set_time(L.h, 10)
+            L.step(3)
+            out.append(L.populations())
+            st.append(L.stats())
+    assert np.array_equal(out[0], out[1])
+    for k in ("E_k", "eps0", "eps_sgs", "theta_mean", "mass"):
+        assert st[0][k] == st[1][k], k
