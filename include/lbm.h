@@ -113,8 +113,8 @@ typedef struct lbm_params {
   int32_t layout;         /* population array in device memory: 1 population-
                              major [19][nz][ny][nxp], 2 row-interleaved
                              [nz][ny][19][nxp] (the 19 x-lines of a cell row are
-                             adjacent: longer contiguous runs for the TMA
-                             kernel); 0: the autotuner picks for the TMA kernel,
+                             adjacent, grouped as lbm_device_ptr states: longer
+                             contiguous runs for the TMA kernel); 0: the autotuner picks for the TMA kernel,
                              population-major otherwise.  Results do not depend
                              on it. */
 } lbm_params;
@@ -281,9 +281,12 @@ int lbm_get_fields(lbm_t h, int32_t inst, double* drho, double* u, double* snorm
 int lbm_get_theta_slice(lbm_t h, int32_t inst, int32_t axis, int32_t index, double* host);
 
 /* Device pointer and size in bytes of the population array of `inst`, for
- * zero-copy inspection (read-only by convention; layout [19][nz][ny][nxp] or
- * [nz][ny][19][nxp] as lbm_kernel_config reports, in the AA order of the
- * current parity). */
+ * zero-copy inspection (read-only by convention), in the AA order of the
+ * current parity and in the layout lbm_kernel_config reports:
+ * [19][nz][ny][nxp] (population-major, slot a at index a) or
+ * [nz][ny][19][nxp] (row-interleaved; the 19 slots of a cell row in the order
+ * 0 1 18 11 3 7 8 13 5 15 16 4 14 17 12 2 6 9 10, grouped by the slot's
+ * (cy, cz)). */
 int lbm_device_ptr(lbm_t h, int32_t inst, void** ptr, size_t* bytes, int32_t* nxp);
 
 /* Effective parameters after derivation: nu0, s_nu0, F0, C of `inst`. */

@@ -286,9 +286,11 @@ int build_tiles(lbm_t h) {
     if (h->layout == 0) {  // [19][nz][ny][nxp]
       d.slot_stride = (int64_t)p.nz * p.ny * I.nxp;
       d.row_stride = I.nxp;
-    } else {  // [nz][ny][19][nxp]
+      d.slot_grouped = 0;
+    } else {  // [nz][ny][19][nxp], slots of a cell row in grouped order
       d.slot_stride = I.nxp;
       d.row_stride = (int64_t)19 * I.nxp;
+      d.slot_grouped = 1;
     }
     d.plane_stride = d.row_stride * p.ny;
     d.rows = R;
@@ -812,6 +814,13 @@ int choose_config(lbm_t h, const lbm_params& p0) {
             if ((lay_req == 1 && lay == 1) || (lay_req == 2 && lay == 0)) continue;
             c.layout = lay;
             cands.push_back(c);
+            // row-interleaved one-x-line tiles also in the runtime stride, where
+            // an odd step moves each slot group of a cell row in one copy
+            if (lay == 1 && R == 1 && c.slot_bytes != 0) {
+              Candidate r = tma_candidate(row_stage, R, s, th, false);
+              r.layout = 1;
+              if (fits(s, r.tile_bytes)) cands.push_back(r);
+            }
           }
         }
       }

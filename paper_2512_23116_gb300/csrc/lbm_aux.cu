@@ -326,11 +326,12 @@ cudaError_t launch_relayout_pair(const InstDesc& d, int precision, bool from_odd
   const size_t plane = row * rows;
   char* s = static_cast<char*>(scratch);
   const char* base = static_cast<const char*>(d.f);
+  const size_t pa = d.slot_grouped ? gpos(a) : a, pb = d.slot_grouped ? gpos(opp(a)) : opp(a);
   // slots a and opp(a), x-line by x-line (row_stride apart in either layout), into dense planes
-  cudaError_t e = cudaMemcpy2DAsync(s, row, base + (size_t)a * d.slot_stride * es, (size_t)d.row_stride * es,
+  cudaError_t e = cudaMemcpy2DAsync(s, row, base + pa * d.slot_stride * es, (size_t)d.row_stride * es,
                                     row, rows, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
-  e = cudaMemcpy2DAsync(s + plane, row, base + (size_t)opp(a) * d.slot_stride * es, (size_t)d.row_stride * es,
+  e = cudaMemcpy2DAsync(s + plane, row, base + pb * d.slot_stride * es, (size_t)d.row_stride * es,
                         row, rows, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
   const int g = grid_for((int64_t)d.nx * d.ny * d.nz);

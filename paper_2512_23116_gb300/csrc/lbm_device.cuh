@@ -37,6 +37,17 @@ __host__ __device__ constexpr int cz(int a) {
   return t[a];
 }
 __host__ __device__ constexpr int opp(int a) { return a == 18 ? 18 : (a ^ 1); }
+
+// Position of population slot a inside a cell row of the row-interleaved
+// layout (and inside a shared-memory tile of the TMA kernel): the slots are
+// grouped by their own (cy, cz), so that each group is what one neighbouring
+// cell row supplies to an odd-step tile.  Groups, in position order: (0,0)
+// {0,1,18}, (-1,-1) {11}, (-1,0) {3,7,8}, (-1,1) {13}, (0,-1) {5,15,16},
+// (0,1) {4,14,17}, (1,-1) {12}, (1,0) {2,6,9}, (1,1) {10}.
+__host__ __device__ constexpr int gpos(int a) {
+  constexpr int t[19] = {0, 1, 15, 4, 11, 8, 16, 5, 6, 17, 18, 3, 14, 7, 12, 9, 10, 13, 2};
+  return t[a];
+}
 __host__ __device__ constexpr double weight(int a) {
   return a == 18 ? 1.0 / 3.0 : (a < 6 ? 1.0 / 18.0 : 1.0 / 36.0);
 }
@@ -323,7 +334,7 @@ __device__ __forceinline__ int64_t cell_off(int x, int y, int z, int ny, int nxp
 
 // Position of population slot a of cell (x, y, z) in an instance's array.
 __device__ __forceinline__ int64_t pop_off(const InstDesc& d, int a, int x, int y, int z) {
-  return a * d.slot_stride + z * d.plane_stride + y * d.row_stride + x;
+  return (d.slot_grouped ? gpos(a) : a) * d.slot_stride + z * d.plane_stride + y * d.row_stride + x;
 }
 
 // Index of the instance owning global tile t (tiles are sorted by instance),

@@ -21,9 +21,11 @@ struct InstDesc {
   int32_t nx, ny, nz, nxp; // nxp: x stride (nx rounded up to the row alignment)
   int32_t row_copy_bytes;  // bytes of one x-line a bulk copy moves (nx cells, 16-byte multiple)
   // Population layout (elements): population-major [19][nz][ny][nxp]
-  // (slot_stride = nz ny nxp, row_stride = nxp) or row-interleaved
-  // [nz][ny][19][nxp] (slot_stride = nxp, row_stride = 19 nxp).
+  // (slot_stride = nz ny nxp, row_stride = nxp, slots in index order) or
+  // row-interleaved [nz][ny][19][nxp] (slot_stride = nxp, row_stride = 19 nxp,
+  // slot a at position gpos(a) of its cell row: slot_grouped = 1).
   int64_t slot_stride, plane_stride, row_stride;
+  int32_t slot_grouped;
   int32_t rows;            // rows (y lines of nx cells) per tile
   int32_t tiles_per_plane; // ceil(ny / rows)
   int64_t tile_begin;      // first global tile of the instance

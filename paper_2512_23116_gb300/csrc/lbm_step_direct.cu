@@ -44,8 +44,10 @@ k_step_direct(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, in
     const InstDesc& d = insts[ii];
     const int nx = d.nx, ny = d.ny, nz = d.nz;
     const int64_t ps = d.slot_stride, pls = d.plane_stride, rs = d.row_stride;
-    // position of cell (x, y, z) within a population slot
+    const bool grouped = d.slot_grouped != 0;
+    // position of cell (x, y, z) within a population slot; offset of slot a
     auto at = [pls, rs](int x, int y, int z) { return z * pls + y * rs + x; };
+    auto slot = [ps, grouped](int a) { return (grouped ? gpos(a) : a) * ps; };
     const int64_t local = t - d.tile_begin;
     const int z = (int)(local / d.tiles_per_plane);
     const int y0 = (int)(local - (int64_t)z * d.tiles_per_plane) * d.rows;
@@ -65,14 +67,14 @@ k_step_direct(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, in
       if (!ODD) {
         const int64_t o = at(x, y, z);
 #pragma unroll
-        for (int a = 0; a < 19; ++a) f[a] = S::load(fb + a * ps + o);
+        for (int a = 0; a < 19; ++a) f[a] = S::load(fb + slot(a) + o);
       } else {
 #pragma unroll
         for (int a = 0; a < 19; ++a) {
           const int xs = cx(a) > 0 ? xm : (cx(a) < 0 ? xp : x);
           const int ys = cy(a) > 0 ? ym : (cy(a) < 0 ? yp : y);
           const int zs = cz(a) > 0 ? zm : (cz(a) < 0 ? zp : z);
-          f[a] = S::load(fb + opp(a) * ps + at(xs, ys, zs));
+          f[a] = S::load(fb + slot(opp(a)) + at(xs, ys, zs));
         }
       }
       const float Fx = d.fx_of_y[y] + d.fconst[0];
@@ -83,14 +85,14 @@ k_step_direct(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, in
         if (!ODD) {
           const int64_t o = at(x, y, z);
 #pragma unroll
-          for (int a = 0; a < 19; ++a) fb[opp(a) * ps + o] = S::pack(f[a]);
+          for (int a = 0; a < 19; ++a) fb[slot(opp(a)) + o] = S::pack(f[a]);
         } else {
 #pragma unroll
           for (int a = 0; a < 19; ++a) {
             const int xd = cx(a) > 0 ? xp : (cx(a) < 0 ? xm : x);
             const int yd = cy(a) > 0 ? yp : (cy(a) < 0 ? ym : y);
             const int zd = cz(a) > 0 ? zp : (cz(a) < 0 ? zm : z);
-            fb[a * ps + at(xd, yd, zd)] = S::pack(f[a]);
+            fb[slot(a) + at(xd, yd, zd)] = S::pack(f[a]);
           }
         }
       }

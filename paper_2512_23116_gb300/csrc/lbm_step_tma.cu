@@ -51,6 +51,19 @@ constexpr int kBarBytes = 128;  // mbarriers + abort flag
 __constant__ int8_t c_seg_opp[19] = {1, 0, 3, 2, 5, 4, 7, 6, 9, 8, 11, 10, 13, 12, 15, 14, 17, 16, 18};
 __constant__ int8_t c_seg_cy[19] = {0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 1, -1, 1, -1, 0, 0, 0, 0, 0};
 __constant__ int8_t c_seg_cz[19] = {0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1, 0};
+// gpos(a) (lbm_device.cuh) for the producer lanes
+__constant__ int8_t c_gpos[19] = {0, 1, 15, 4, 11, 8, 16, 5, 6, 17, 18, 3, 14, 7, 12, 9, 10, 13, 2};
+// The 9 slot groups of a cell row in position order: first position, length
+// and the slots' own (cy, cz) -- an odd-step tile at row (y, z) reads group g
+// whole from cell row (y + cy_g, z + cz_g).
+__constant__ int8_t c_grp_start[9] = {0, 3, 4, 7, 8, 11, 14, 15, 18};
+__constant__ int8_t c_grp_len[9] = {3, 1, 3, 1, 3, 3, 1, 3, 1};
+__constant__ int8_t c_grp_cy[9] = {0, -1, -1, -1, 0, 0, 1, 1, 1};
+__constant__ int8_t c_grp_cz[9] = {0, -1, 0, 1, -1, 1, -1, 0, 1};
+
+// Shared-memory position of segment j of a tile (what its cells read as f_j):
+// the grouped position of the slot it is copied from.
+__host__ __device__ constexpr int spos(int j, bool odd) { return gpos(odd ? opp(j) : j); }
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -217,8 +230,10 @@ __device__ __forceinline__ SegRows seg_rows(const InstDesc& d, const TileGeom& g
   const char* base = static_cast<const char*>(d.f);
   SegRows s;
   s.step = d.row_stride * es;
+  const int slot = ODD ? c_seg_opp[j] : j;
+  const int64_t spos_g = d.slot_grouped ? c_gpos[slot] : slot;  // its position in global memory
   if (!ODD) {
-    s.plane = base + (j * d.slot_stride + g.z * d.plane_stride) * es;
+    s.plane = base + (spos_g * d.slot_stride + g.z * d.plane_stride) * es;
     s.ys = g.y0;
     s.first = g.rows;
   } else {
@@ -226,7 +241,7 @@ __device__ __forceinline__ SegRows seg_rows(const InstDesc& d, const TileGeom& g
     zs = zs < 0 ? zs + d.nz : (zs >= d.nz ? zs - d.nz : zs);
     int ys = g.y0 - c_seg_cy[j];
     ys = ys < 0 ? ys + d.ny : (ys >= d.ny ? ys - d.ny : ys);
-    s.plane = base + (c_seg_opp[j] * d.slot_stride + zs * d.plane_stride) * es;
+    s.plane = base + (spos_g * d.slot_stride + zs * d.plane_stride) * es;
     s.ys = ys;
     s.first = min(g.rows, d.ny - ys);
   }
@@ -245,7 +260,7 @@ __device__ __forceinline__ void load_segment(const InstDesc& d, const TileGeom& 
   const uint32_t row_bytes = (uint32_t)d.nxp * (uint32_t)sizeof(T);
   const uint32_t seg_bytes = SLOT ? (uint32_t)SLOT : row_bytes * (uint32_t)d.rows;
   const SegRows sr = seg_rows<T, ODD>(d, g, j);
-  const uint32_t dst = buf + (uint32_t)j * seg_bytes;
+  const uint32_t dst = buf + (uint32_t)c_gpos[ODD ? c_seg_opp[j] : j] * seg_bytes;  // spos(j, ODD)
   if ((uint32_t)d.row_copy_bytes == row_bytes && sr.step == (int64_t)row_bytes) {
     bulk_load(dst, sr.plane + (int64_t)sr.ys * row_bytes, (uint32_t)sr.first * row_bytes, bar);
     if (sr.first < g.rows)
@@ -265,7 +280,7 @@ __device__ __forceinline__ void store_segment(const InstDesc& d, const TileGeom&
   const uint32_t row_bytes = (uint32_t)d.nxp * (uint32_t)sizeof(T);
   const uint32_t seg_bytes = SLOT ? (uint32_t)SLOT : row_bytes * (uint32_t)d.rows;
   const SegRows sr = seg_rows<T, ODD>(d, g, j);
-  const uint32_t src = buf + (uint32_t)j * seg_bytes;
+  const uint32_t src = buf + (uint32_t)c_gpos[ODD ? c_seg_opp[j] : j] * seg_bytes;  // spos(j, ODD)
   if ((uint32_t)d.row_copy_bytes == row_bytes && sr.step == (int64_t)row_bytes) {
     bulk_store(const_cast<char*>(sr.plane) + (int64_t)sr.ys * row_bytes, src, (uint32_t)sr.first * row_bytes);
     if (sr.first < g.rows)
@@ -279,6 +294,63 @@ __device__ __forceinline__ void store_segment(const InstDesc& d, const TileGeom&
     }
   }
   bulk_commit();
+}
+
+// Odd steps of the row-interleaved layout with one-x-line tiles in the runtime
+// stride (shared-memory positions one x-line apart, like the global ones):
+// the tile's 19 segments are the 9 slot groups of its 9 neighbouring cell
+// rows, each adjacent in global and in shared memory, so producer lane g < 9
+// moves group g in one piece.
+template <typename T, bool ODD, int SLOT>
+__device__ __forceinline__ bool grouped_copies(const InstDesc& d) {
+  return ODD && SLOT == 0 && d.slot_grouped && d.rows == 1 &&
+         (uint32_t)d.row_copy_bytes == (uint32_t)d.nxp * (uint32_t)sizeof(T);
+}
+
+template <typename T>
+__device__ __forceinline__ const char* group_src(const InstDesc& d, const TileGeom& g, int k) {
+  int zs = g.z + c_grp_cz[k];
+  zs = zs < 0 ? zs + d.nz : (zs >= d.nz ? zs - d.nz : zs);
+  int ys = g.y0 + c_grp_cy[k];
+  ys = ys < 0 ? ys + d.ny : (ys >= d.ny ? ys - d.ny : ys);
+  return static_cast<const char*>(d.f) +
+         (c_grp_start[k] * d.slot_stride + zs * d.plane_stride + ys * d.row_stride) * (int64_t)sizeof(T);
+}
+
+template <typename T>
+__device__ __forceinline__ void load_group(const InstDesc& d, const TileGeom& g, int k, uint32_t buf, uint32_t bar) {
+  const uint32_t row_bytes = (uint32_t)d.nxp * (uint32_t)sizeof(T);
+  bulk_load(buf + (uint32_t)c_grp_start[k] * row_bytes, group_src<T>(d, g, k), (uint32_t)c_grp_len[k] * row_bytes,
+            bar);
+}
+
+template <typename T>
+__device__ __forceinline__ void store_group(const InstDesc& d, const TileGeom& g, int k, uint32_t buf) {
+  const uint32_t row_bytes = (uint32_t)d.nxp * (uint32_t)sizeof(T);
+  bulk_store(const_cast<char*>(group_src<T>(d, g, k)), buf + (uint32_t)c_grp_start[k] * row_bytes,
+             (uint32_t)c_grp_len[k] * row_bytes);
+  bulk_commit();
+}
+
+// Producer lane `lane`: its share of the loads / stores of a tile (a slot
+// group or a segment, or nothing).
+template <typename T, bool ODD, int SLOT>
+__device__ __forceinline__ void tile_load(const InstDesc& d, const TileGeom& g, int lane, uint32_t buf,
+                                          uint32_t bar) {
+  if (grouped_copies<T, ODD, SLOT>(d)) {
+    if (lane < 9) load_group<T>(d, g, lane, buf, bar);
+  } else if (lane < 19) {
+    load_segment<T, ODD, SLOT>(d, g, lane, buf, bar);
+  }
+}
+
+template <typename T, bool ODD, int SLOT>
+__device__ __forceinline__ void tile_store(const InstDesc& d, const TileGeom& g, int lane, uint32_t buf) {
+  if (grouped_copies<T, ODD, SLOT>(d)) {
+    if (lane < 9) store_group<T>(d, g, lane, buf);
+  } else if (lane < 19) {
+    store_segment<T, ODD, SLOT>(d, g, lane, buf);
+  }
 }
 
 // Bytes that the bulk loads of one tile deliver.
@@ -316,7 +388,7 @@ __device__ __forceinline__ void collide_tile(const CellLoop& cl, int ncell, cons
 #pragma unroll
     for (int a = 0; a < 19; ++a) {
       const int xs = ODD ? (cx(a) > 0 ? xm : (cx(a) < 0 ? xp : x)) : x;
-      f[a] = S::cvt(row[a * seg + xs]);
+      f[a] = S::cvt(row[spos(a, ODD) * seg + xs]);
     }
     const float Fx = __ldg(fx + r) + cl.fx_const;
     const float Fz = fz_table[x];
@@ -325,7 +397,7 @@ __device__ __forceinline__ void collide_tile(const CellLoop& cl, int ncell, cons
 #pragma unroll
     for (int a = 0; a < 19; ++a) {
       const int xd = ODD ? (cx(a) > 0 ? xp : (cx(a) < 0 ? xm : x)) : x;
-      row[opp(a) * seg + xd] = S::pack(f[a]);
+      row[spos(opp(a), ODD) * seg + xd] = S::pack(f[a]);
     }
     if (MODE == MODE_STEP_STATS) acc.add(cd, Fx, Fy, Fz, cl.C);
     x += cl.dx;
@@ -368,7 +440,6 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
     const int64_t first = tile_lo + blockIdx.x;
     const int64_t stride = gridDim.x;
     const int ntiles = first < tile_hi ? (int)((tile_hi - 1 - first) / stride) + 1 : 0;
-    const bool seg_lane = lane < 19;
     // test hook: block 0 leaves the barrier of its first tile without an
     // arrival, so that its consumers' bounded wait runs out
     const bool withheld = withhold_first_load && blockIdx.x == 0;
@@ -383,7 +454,7 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
         const uint32_t bar = bar_full + 8u * loaded;
         if (lane == 0) mbar_expect_tx(bar, tile_bytes_of(d, g, (int)sizeof(T)));
         __syncwarp();
-        if (seg_lane) load_segment<T, ODD, SLOT>(d, g, lane, buf0 + (uint32_t)loaded * tile_bytes, bar);
+        tile_load<T, ODD, SLOT>(d, g, lane, buf0 + (uint32_t)loaded * tile_bytes, bar);
       }
       walker_next(wl, insts, ninst, stride, tile_hi);
     }
@@ -405,7 +476,7 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
       }
       const TileGeom g = walker_geom(ws);
       const uint32_t buf = buf0 + (uint32_t)s * tile_bytes;
-      if (seg_lane) store_segment<T, ODD, SLOT>(insts[g.ii], g, lane, buf);
+      tile_store<T, ODD, SLOT>(insts[g.ii], g, lane, buf);
       walker_next(ws, insts, ninst, stride, tile_hi);
       if (loaded < ntiles) {
         const TileGeom gn = walker_geom(wl);
@@ -414,11 +485,13 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
         const uint32_t bar = bar_full + 8u * s;
         if (lane == 0) mbar_expect_tx(bar, tile_bytes_of(dn, gn, (int)sizeof(T)));
         __syncwarp();
-        if (seg_lane) {
-          // this lane's segment region is free once its own store has read it
-          bulk_wait_read_all();
-          load_segment<T, ODD, SLOT>(dn, gn, lane, buf, bar);
-        }
+        // a lane's region is free once its own store has read it; when the
+        // next tile belongs to another instance the regions of the lanes may
+        // differ (tile rows, slot groups), so then every lane's store must
+        // have read the stage first
+        bulk_wait_read_all();
+        if (gn.ii != g.ii) __syncwarp();
+        tile_load<T, ODD, SLOT>(dn, gn, lane, buf, bar);
         ++loaded;
       }
       if (++s == stages) {

@@ -2,7 +2,8 @@
 
 The 800^3 forced-HIT DNS-shape workload (FP32, FP16- and BF16-shifted storage) is
 far beyond what the oracle can run, so sampled cells are checked one by one:
-the population array is read in place through lbm_device_ptr (zero-copy), the
+the population array is read in place through lbm_device_ptr (zero-copy, in
+the layout lbm_kernel_config reports), the
 19 pre-collision populations of each sampled cell are taken from the AA layout,
 one step is run, and the post-collision values the kernel stored for that cell
 are compared with the oracle's single-cell collision (Eq. mrt_les_guo).
@@ -35,6 +36,15 @@ def _populations_view(torch, lbm, L, dev, typestr):
         A = A.view(torch.bfloat16)
     assert A.numel() * A.element_size() == nbytes
     return A if L.config()["layout"] == 1 else A.permute(2, 0, 1, 3)
+
+
+# Position of population slot a inside a cell row of the row-interleaved array
+# (the order include/lbm.h documents for lbm_device_ptr)
+GPOS = [0, 1, 15, 4, 11, 8, 16, 5, 6, 17, 18, 3, 14, 7, 12, 9, 10, 13, 2]
+
+
+def _slot_map(lbm, L):
+    return GPOS if L.config()["layout"] == 2 else list(range(19))
 
 
 class _CudaArray:
@@ -77,6 +87,7 @@ def test_800_cubed_sampled_cells_match_oracle(gpu_lib, precision):
             L.step(2)
             L.sync()
             A = _populations_view(torch, lbm, L, dev, ["<f4", "<f2", "bf16"][precision])
+            sm = _slot_map(lbm, L)  # slot -> index along A's first axis
             X = torch.as_tensor(cells[:, 0], device=dev)
             Y = torch.as_tensor(cells[:, 1], device=dev)
             Z = torch.as_tensor(cells[:, 2], device=dev)
@@ -85,23 +96,23 @@ def test_800_cubed_sampled_cells_match_oracle(gpu_lib, precision):
                 pre = torch.empty((19, len(cells)), dtype=torch.float64, device=dev)
                 for q in range(19):
                     if parity == "even":
-                        pre[q] = A[q, Z, Y, X].double()
+                        pre[q] = A[sm[q], Z, Y, X].double()
                     else:
                         xs_ = (X - int(c[q][0])) % N
                         ys_ = (Y - int(c[q][1])) % N
                         zs_ = (Z - int(c[q][2])) % N
-                        pre[q] = A[opp[q], zs_, ys_, xs_].double()
+                        pre[q] = A[sm[opp[q]], zs_, ys_, xs_].double()
                 L.step(1)
                 L.sync()
                 post = torch.empty_like(pre)
                 for q in range(19):
                     if parity == "even":
-                        post[q] = A[opp[q], Z, Y, X].double()
+                        post[q] = A[sm[opp[q]], Z, Y, X].double()
                     else:
                         xd = (X + int(c[q][0])) % N
                         yd = (Y + int(c[q][1])) % N
                         zd = (Z + int(c[q][2])) % N
-                        post[q] = A[q, zd, yd, xd].double()
+                        post[q] = A[sm[q], zd, yd, xd].double()
                 pre_h = pre.cpu().numpy()
                 post_h = post.cpu().numpy()
                 want = np.empty_like(post_h)

@@ -362,25 +362,59 @@ def test_tma_shared_memory_layouts_agree(gpu_lib, precision):
 @pytest.mark.parametrize("kind", KINDS)
 def test_population_layouts_agree(gpu_lib, kind):
     """The population-major and row-interleaved arrays give bitwise-equal
-    canonical populations and statistics (same kernel configuration), through
-    even and odd steps, a statistics step and a parity change."""
+    canonical populations and statistics (same kernel), through even and odd
+    steps, statistics steps and a parity change.  For the TMA kernel the
+    configurations cover compile-time slots (2 stages) and the runtime stride
+    with one-x-line tiles (4 stages), where odd steps of the row-interleaved
+    array copy each slot group of a cell row in one piece."""
     lbm = gpu_lib
     nx, ny, nz = 24, 10, 7
     u = synthetic.random_solenoidal(nx, ny, nz, seed=11)
+    if kind == 2:
+        cfgs = [dict(kernel=2, tile_rows=2, stages=2, threads=256), dict(kernel=2, tile_rows=1, stages=4, threads=256),
+                dict(kernel=2, tile_rows=1, stages=3, threads=384)]
+    else:
+        cfgs = [dict(kernel=1, tile_rows=1, threads=256)]
     out, st = [], []
-    for layout in (1, 2):
-        cfg = dict(kernel=2, tile_rows=2, stages=2, threads=256) if kind == 2 else dict(kernel=1, tile_rows=1,
-                                                                                       threads=256)
-        p = lbm.make_params(nx, ny, nz, nu0=0.002, cs=0.13, f0=1e-4, force_mode=lbm.LBM_FORCE_PAPER_SIN,
-                            stats_every=4, layout=layout, **cfg)
-        with lbm.Lattice(p) as L:
-            assert L.config()["layout"] == layout
-            L.init(lbm.LBM_INIT_VELOCITY, u=u)
-            L.step(9)
-            lbm.lbm_set_time(L.h, 10)
-            L.step(3)
-            out.append(L.populations())
-            st.append(L.stats())
-    assert np.array_equal(out[0], out[1])
-    for k in ("E_k", "eps0", "eps_sgs", "theta_mean", "mass"):
-        assert st[0][k] == st[1][k], k
+    for cfg in cfgs:
+        for layout in (1, 2):
+            p = lbm.make_params(nx, ny, nz, nu0=0.002, cs=0.13, f0=1e-4, force_mode=lbm.LBM_FORCE_PAPER_SIN,
+                                stats_every=4, layout=layout, **cfg)
+            with lbm.Lattice(p) as L:
+                c = L.config()
+                assert c["layout"] == layout and c["tile_rows"] == cfg["tile_rows"]
+                L.init(lbm.LBM_INIT_VELOCITY, u=u)
+                L.step(9)
+                lbm.lbm_set_time(L.h, 10)
+                L.step(3)
+                out.append(L.populations())
+                st.append(L.stats())
+    for o in out[1:]:
+        assert np.array_equal(out[0], o)
+    for x in st[1:]:
+        for k in ("E_k", "eps0", "eps_sgs", "theta_mean", "mass"):
+            assert x[k] == st[0][k], k
+
+
+def test_grouped_copies_across_uneven_instances(gpu_lib):
+    """A batch of instances of different x-line lengths in the row-interleaved
+    array with one-x-line tiles in the runtime stride (grouped odd-step copies):
+    the producer's shared-memory regions change at every instance boundary.
+    Each instance matches its own oracle run."""
+    lbm = gpu_lib
+    shapes = [(6, 8, 40), (9, 5, 12), (4, 7, 64)]
+    params, refs, inits = [], [], []
+    for i, (nz, ny, nx) in enumerate(shapes):
+        params.append(lbm.make_params(nx, ny, nz, nu0=0.004, cs=0.13, f0=1e-4, force_mode=lbm.LBM_FORCE_PAPER_SIN,
+                                      kernel=2, tile_rows=1, stages=4, threads=256, layout=2))
+        refs.append(oracle.OracleLBM(nx, ny, nz, 0.004, 0.13, oracle.FORCE_PAPER_SIN, F0=1e-4))
+        inits.append(synthetic.random_solenoidal(nx, ny, nz, seed=30 + i))
+    with lbm.Lattice(params) as g:
+        assert g.config()["layout"] == 2
+        for i in range(len(shapes)):
+            g.init(lbm.LBM_INIT_VELOCITY, u=inits[i], inst=i)
+        g.step(17)
+        for i in range(len(shapes)):
+            refs[i].init_equilibrium(inits[i])
+            refs[i].step(17)
+            assert full_f_rel_error(g.populations(inst=i), refs[i].populations()) <= 1e-5, i
