@@ -252,14 +252,16 @@ def time_steps(lbm, lat, stream, steps, warmup, dist):
 def run_case(lbm, n, precision, C, nu0, steps, warmup, device, stream, u_dev, dist, clocks=None,
              config="", shape=None, row_align=0, layout=0):
     """Create, initialise from the device velocity, time `steps` steps."""
-    kind = rows = stages = threads = 0
+    kind = rows = stages = threads = slots = 0
     if config:
-        kind, rows, stages, threads = (int(v) for v in config.split(","))
+        vals = [int(v) for v in config.split(",")]
+        kind, rows, stages, threads = vals[:4]
+        slots = vals[4] if len(vals) > 4 else 0
     nx, ny, nz = shape if shape else (n, n, n)
     p = lbm.make_params(nx, ny, nz, precision=precision, nu0=nu0, cs=C, f0=CF * U0 * U0 / nx,
                         force_mode=lbm.LBM_FORCE_PAPER_SIN, device=device, stream=stream.cuda_stream,
                         kernel=kind, tile_rows=rows, stages=stages, threads=threads, row_align=row_align,
-                        layout=layout)
+                        layout=layout, tma_slots=slots)
     lat = lbm.Lattice(p)
     lat.init(lbm.LBM_INIT_VELOCITY, u=u_dev)
     if clocks is not None:
@@ -569,7 +571,7 @@ def main():
     ap.add_argument("--layout", type=int, default=0, choices=[0, 1, 2],
                     help="population array of an --only-step run: 1 population-major, 2 row-interleaved, 0 autotuned")
     ap.add_argument("--config", default="",
-                    help="kind,tile_rows,stages,threads: a fixed kernel configuration (no autotuning)")
+                    help="kind,tile_rows,stages,threads[,tma_slots]: a fixed kernel configuration (no autotuning)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -117,6 +117,12 @@ typedef struct lbm_params {
                              contiguous runs for the TMA kernel); 0: the autotuner picks for the TMA kernel,
                              population-major otherwise.  Results do not depend
                              on it. */
+  int32_t tma_slots;      /* shared-memory tiles of the TMA kernel: 0 compile-time
+                             slots when the tile fits one (the autotuner also
+                             tries the runtime stride), 1 always the runtime
+                             stride (x-lines of a tile packed; with one-x-line
+                             tiles of the row-interleaved array an odd step
+                             copies each slot group of a cell row in one piece) */
 } lbm_params;
 
 /* Domain statistics of one instance at one time (all FP64 sums on the device). */
@@ -294,9 +300,11 @@ int lbm_get_params(lbm_t h, int32_t inst, double* nu0, double* s_nu0, double* f0
 
 /* Kernel chosen by the autotuner: kind (1 direct, 2 TMA bulk), tile rows,
  * pipeline stages, threads per block, blocks per SM, population layout (1
- * population-major, 2 row-interleaved).  Any pointer may be NULL. */
+ * population-major, 2 row-interleaved), shared-memory slot bytes of the TMA
+ * tiles (0: runtime stride).  Any pointer may be NULL. */
 int lbm_kernel_config(lbm_t h, int32_t* kind, int32_t* tile_rows, int32_t* stages,
-                      int32_t* threads, int32_t* blocks_per_sm, int32_t* layout);
+                      int32_t* threads, int32_t* blocks_per_sm, int32_t* layout,
+                      int32_t* slot_bytes);
 
 /* Test hook for the failure path (no counterpart in the paper): the next
  * TMA-kernel step launch of `h` runs with every device-side wait bounded by

@@ -57,6 +57,7 @@ class LbmParams(ctypes.Structure):
         ("kernel", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
         ("stages", ctypes.c_int32), ("threads", ctypes.c_int32),
         ("row_align", ctypes.c_int32), ("strain_mode", ctypes.c_int32), ("layout", ctypes.c_int32),
+        ("tma_slots", ctypes.c_int32),
     ]
 
 
@@ -153,7 +154,7 @@ def load():
         "lbm_device_ptr": ([H, i32, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_size_t),
                             ctypes.POINTER(i32)], ctypes.c_int),
         "lbm_get_params": ([H, i32, _D, _D, _D, _D], ctypes.c_int),
-        "lbm_kernel_config": ([H] + [ctypes.POINTER(i32)] * 6, ctypes.c_int),
+        "lbm_kernel_config": ([H] + [ctypes.POINTER(i32)] * 7, ctypes.c_int),
         "lbm_last_error": ([H], ctypes.c_char_p),
         "lbm_version": ([], ctypes.c_char_p),
         "lbm_structure_functions_noalloc": ([ctypes.c_void_p, i32, i32, i32, ctypes.POINTER(i32), i32,
@@ -191,7 +192,8 @@ def _ptr(a: np.ndarray):
 def make_params(nx, ny=None, nz=None, *, precision=LBM_FP32, re=0.0, u0=0.0, nu0=0.0, cs=0.0,
                 cf=0.2, f0=0.0, body_force=(0.0, 0.0, 0.0), force_mode=LBM_FORCE_NONE,
                 stats_every=0, hist_bins=0, hist_max=0.0, device=0, stream=None, kernel=0,
-                tile_rows=0, stages=0, threads=0, row_align=0, strain_mode=0, layout=0) -> LbmParams:
+                tile_rows=0, stages=0, threads=0, row_align=0, strain_mode=0, layout=0,
+                tma_slots=0) -> LbmParams:
     p = LbmParams()
     p.nx, p.ny, p.nz = nx, nx if ny is None else ny, nx if nz is None else nz
     p.precision = precision
@@ -206,6 +208,7 @@ def make_params(nx, ny=None, nz=None, *, precision=LBM_FP32, re=0.0, u0=0.0, nu0
     p.row_align = row_align
     p.strain_mode = strain_mode
     p.layout = layout
+    p.tma_slots = tma_slots
     return p
 
 
@@ -356,9 +359,10 @@ def lbm_get_params(h, inst: int = 0) -> dict:
 
 
 def lbm_kernel_config(h) -> dict:
-    v = [ctypes.c_int32() for _ in range(6)]
+    v = [ctypes.c_int32() for _ in range(7)]
     _check(h, load().lbm_kernel_config(h, *[ctypes.byref(x) for x in v]))
-    return dict(zip(("kind", "tile_rows", "stages", "threads", "blocks_per_sm", "layout"), [x.value for x in v]))
+    return dict(zip(("kind", "tile_rows", "stages", "threads", "blocks_per_sm", "layout", "slot_bytes"),
+                    [x.value for x in v]))
 
 
 def lbm_structure_functions_noalloc(u, r, sp, stream=None) -> None:

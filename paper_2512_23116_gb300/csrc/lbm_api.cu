@@ -160,6 +160,7 @@ int validate(const lbm_params& p, std::string& why) {
   if (p.tile_rows < 0) { why = "tile_rows < 0"; return LBM_ERR_INVALID_ARG; }
   if (p.strain_mode < 0 || p.strain_mode > 1) { why = "strain_mode must be 0 or 1"; return LBM_ERR_INVALID_ARG; }
   if (p.layout < 0 || p.layout > 2) { why = "layout must be 0, 1 or 2"; return LBM_ERR_INVALID_ARG; }
+  if (p.tma_slots < 0 || p.tma_slots > 1) { why = "tma_slots must be 0 or 1"; return LBM_ERR_INVALID_ARG; }
   if (p.row_align != 0 && (p.row_align < 16 || p.row_align > 65536 || (p.row_align & (p.row_align - 1)))) {
     why = "row_align must be 0 or a power of two in [16, 65536]";
     return LBM_ERR_INVALID_ARG;
@@ -786,8 +787,9 @@ int choose_config(lbm_t h, const lbm_params& p0) {
   // a fully specified configuration skips the autotuner
   if (requested_kind == 1 && requested_rows > 0 && p0.threads > 0)
     return apply_candidate(h, {1, p0.threads, 0, 0, requested_rows, 0, lay_fixed});
+  const bool allow_slots = p0.tma_slots == 0;
   if (requested_kind == 2 && requested_rows > 0 && p0.threads > 0 && p0.stages > 0) {
-    Candidate c = tma_candidate(row_stage, requested_rows, p0.stages, p0.threads);
+    Candidate c = tma_candidate(row_stage, requested_rows, p0.stages, p0.threads, allow_slots);
     if (!fits(p0.stages, c.tile_bytes)) c = tma_candidate(row_stage, requested_rows, p0.stages, p0.threads, false);
     if (!tma_ok || !fits(p0.stages, c.tile_bytes))
       return fail(h, LBM_ERR_UNSUPPORTED, "requested TMA stages do not fit shared memory");
@@ -807,7 +809,7 @@ int choose_config(lbm_t h, const lbm_params& p0) {
       if ((row_stage * R + 15) / 16 * 16 > 96 * 1024) break;
       for (int s : stage_opts) {
         for (int th : thread_opts) {
-          Candidate c = tma_candidate(row_stage, R, s, th);
+          Candidate c = tma_candidate(row_stage, R, s, th, allow_slots);
           if (!fits(s, c.tile_bytes)) c = tma_candidate(row_stage, R, s, th, false);
           if (!fits(s, c.tile_bytes)) continue;
           for (int lay = 0; lay < 2; ++lay) {
@@ -826,7 +828,7 @@ int choose_config(lbm_t h, const lbm_params& p0) {
       }
     }
     if (requested_kind == 2 && cands.empty() && fits(2, (row_stage + 15) / 16 * 16)) {
-      Candidate c = tma_candidate(row_stage, 1, 2, 256);
+      Candidate c = tma_candidate(row_stage, 1, 2, 256, allow_slots);
       c.layout = lay_fixed;
       cands.push_back(c);
     }
@@ -1273,7 +1275,8 @@ LBM_API int lbm_get_params(lbm_t h, int32_t inst, double* nu0, double* s_nu0, do
 }
 
 LBM_API int lbm_kernel_config(lbm_t h, int32_t* kind, int32_t* tile_rows, int32_t* stages,
-                              int32_t* threads, int32_t* blocks_per_sm, int32_t* layout) {
+                              int32_t* threads, int32_t* blocks_per_sm, int32_t* layout,
+                              int32_t* slot_bytes) {
   if (!h) return fail(nullptr, LBM_ERR_INVALID_ARG, "null handle");
   if (kind) *kind = h->kind;
   if (tile_rows) *tile_rows = h->inst.empty() ? 0 : h->inst[0].rows;
@@ -1281,6 +1284,7 @@ LBM_API int lbm_kernel_config(lbm_t h, int32_t* kind, int32_t* tile_rows, int32_
   if (threads) *threads = h->threads;
   if (blocks_per_sm) *blocks_per_sm = h->bps;
   if (layout) *layout = h->layout == 1 ? 2 : 1;
+  if (slot_bytes) *slot_bytes = h->kind == 2 ? h->slot_bytes : 0;
   return LBM_OK;
 }
 

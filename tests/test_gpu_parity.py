@@ -372,7 +372,8 @@ def test_population_layouts_agree(gpu_lib, kind):
     u = synthetic.random_solenoidal(nx, ny, nz, seed=11)
     if kind == 2:
         cfgs = [dict(kernel=2, tile_rows=2, stages=2, threads=256), dict(kernel=2, tile_rows=1, stages=4, threads=256),
-                dict(kernel=2, tile_rows=1, stages=3, threads=384)]
+                dict(kernel=2, tile_rows=1, stages=3, threads=384),
+                dict(kernel=2, tile_rows=1, stages=2, threads=256, tma_slots=1)]
     else:
         cfgs = [dict(kernel=1, tile_rows=1, threads=256)]
     out, st = [], []
@@ -383,6 +384,8 @@ def test_population_layouts_agree(gpu_lib, kind):
             with lbm.Lattice(p) as L:
                 c = L.config()
                 assert c["layout"] == layout and c["tile_rows"] == cfg["tile_rows"]
+                if kind == 2:  # compile-time slots exactly where they apply
+                    assert (c["slot_bytes"] == 0) == (cfg["stages"] == 4 or cfg.get("tma_slots", 0) == 1)
                 L.init(lbm.LBM_INIT_VELOCITY, u=u)
                 L.step(9)
                 lbm.lbm_set_time(L.h, 10)
