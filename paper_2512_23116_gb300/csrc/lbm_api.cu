@@ -328,7 +328,7 @@ LaunchArgs base_args(lbm_t h) {
   la.grid = h->grid;
   la.threads = h->threads;
   la.stages = h->stages;
-  la.slot_bytes = h->slot_bytes;
+  la.slot_bytes = (h->kind == 2 && h->slot_bytes == 0 && h->layout == 1) ? kSlotGrouped : h->slot_bytes;
   la.smem_bytes = h->smem;
   la.tile_bytes_max = h->tile_bytes_max;
   la.err = h->d_err;
@@ -717,7 +717,8 @@ int apply_candidate(lbm_t h, const Candidate& c) {
     for (const Inst& I : h->inst) max_nx = std::max(max_nx, I.p.nx);
     h->smem = tma_smem_bytes(c.stages, c.tile_bytes, max_nx);
     if (tma_prepare(h->precision, h->smem) != cudaSuccess) return LBM_ERR_UNSUPPORTED;
-    h->bps = tma_max_blocks_per_sm(h->precision, h->slot_bytes, c.threads, h->smem);
+    h->bps = tma_max_blocks_per_sm(h->precision, (h->slot_bytes == 0 && h->layout == 1) ? kSlotGrouped : h->slot_bytes,
+                                   c.threads, h->smem);
   } else {
     h->smem = 0;
     h->bps = direct_max_blocks_per_sm(h->precision, c.threads);

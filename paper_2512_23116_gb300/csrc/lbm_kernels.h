@@ -21,7 +21,8 @@ struct LaunchArgs {
   int grid, threads;
   // TMA kernel configuration
   int stages;
-  int slot_bytes;          // shared-memory slot per population segment: kSlot3, kSlot2 or 0 (rows x nxp)
+  int slot_bytes;          // shared-memory slot per population segment: kSlot3, kSlot2, or the runtime
+                           // stride rows x nxp: 0, or kSlotGrouped for the row-interleaved array
   int smem_bytes;          // dynamic shared memory of the TMA kernel
   int tile_bytes_max;      // bytes of one stage (19 segments)
   uint32_t* err;           // device error word
@@ -39,6 +40,9 @@ int direct_max_blocks_per_sm(int precision, int threads);
 // size) <= slot.
 constexpr int kSlot3 = 3840;
 constexpr int kSlot2 = 5760;
+// Runtime-stride tiles of the row-interleaved array: segments at the grouped
+// positions of their slots (odd steps then copy whole slot groups).
+constexpr int kSlotGrouped = -1;
 
 cudaError_t launch_step_tma(const LaunchArgs& la, cudaStream_t st);
 // Dynamic shared memory of the TMA kernel: barriers, `stages` tile buffers and

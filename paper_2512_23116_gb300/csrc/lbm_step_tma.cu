@@ -61,9 +61,18 @@ __constant__ int8_t c_grp_len[9] = {3, 1, 3, 1, 3, 3, 1, 3, 1};
 __constant__ int8_t c_grp_cy[9] = {0, -1, -1, -1, 0, 0, 1, 1, 1};
 __constant__ int8_t c_grp_cz[9] = {0, -1, 0, 1, -1, 1, -1, 0, 1};
 
-// Shared-memory position of segment j of a tile (what its cells read as f_j):
-// the grouped position of the slot it is copied from.
-__host__ __device__ constexpr int spos(int j, bool odd) { return gpos(odd ? opp(j) : j); }
+// Shared-memory position of segment j of a tile (what its cells read as f_j).
+// SLOT = kSlotGrouped (runtime stride, row-interleaved array): the grouped
+// position of the slot it is copied from, so that a slot group of a cell row
+// lands in one piece; otherwise position j.
+template <int SLOT>
+__host__ __device__ constexpr int spos(int j, bool odd) {
+  return SLOT == kSlotGrouped ? gpos(odd ? opp(j) : j) : j;
+}
+// Bytes between segment positions of a stage: the compile-time slot, or the
+// runtime stride of `rows` x-lines.
+template <int SLOT>
+__host__ __device__ constexpr bool slotted() { return SLOT > 0; }
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -224,8 +233,22 @@ struct SegRows {
   int ys, first;
 };
 
+// The per-instance fields the producer's copies need, kept in registers (the
+// producer is on the critical path of every stage turnaround: no descriptor
+// loads per tile).
+struct SegInst {
+  const void* f;
+  int64_t slot_stride, plane_stride, row_stride;
+  int32_t nxp, ny, nz, rows, row_copy_bytes, slot_grouped;
+};
+
+__device__ __forceinline__ SegInst seg_inst(const InstDesc& d) {
+  return SegInst{d.f, d.slot_stride, d.plane_stride, d.row_stride, d.nxp, d.ny, d.nz, d.rows,
+                 d.row_copy_bytes, d.slot_grouped};
+}
+
 template <typename T, bool ODD>
-__device__ __forceinline__ SegRows seg_rows(const InstDesc& d, const TileGeom& g, int j) {
+__device__ __forceinline__ SegRows seg_rows(const SegInst& d, const TileGeom& g, int j) {
   const int64_t es = (int64_t)sizeof(T);
   const char* base = static_cast<const char*>(d.f);
   SegRows s;
@@ -255,12 +278,13 @@ __device__ __forceinline__ SegRows seg_rows(const InstDesc& d, const TileGeom& g
 // on its own, live cells only.  Lane 0 must have posted the tile's expected
 // bytes.
 template <typename T, bool ODD, int SLOT>
-__device__ __forceinline__ void load_segment(const InstDesc& d, const TileGeom& g, int j, uint32_t buf,
+__device__ __forceinline__ void load_segment(const SegInst& d, const TileGeom& g, int j, uint32_t buf,
                                              uint32_t bar) {
   const uint32_t row_bytes = (uint32_t)d.nxp * (uint32_t)sizeof(T);
-  const uint32_t seg_bytes = SLOT ? (uint32_t)SLOT : row_bytes * (uint32_t)d.rows;
+  const uint32_t seg_bytes = slotted<SLOT>() ? (uint32_t)SLOT : row_bytes * (uint32_t)d.rows;
   const SegRows sr = seg_rows<T, ODD>(d, g, j);
-  const uint32_t dst = buf + (uint32_t)c_gpos[ODD ? c_seg_opp[j] : j] * seg_bytes;  // spos(j, ODD)
+  const uint32_t pos = SLOT == kSlotGrouped ? (uint32_t)c_gpos[ODD ? c_seg_opp[j] : j] : (uint32_t)j;  // spos
+  const uint32_t dst = buf + pos * seg_bytes;
   if ((uint32_t)d.row_copy_bytes == row_bytes && sr.step == (int64_t)row_bytes) {
     bulk_load(dst, sr.plane + (int64_t)sr.ys * row_bytes, (uint32_t)sr.first * row_bytes, bar);
     if (sr.first < g.rows)
@@ -276,11 +300,12 @@ __device__ __forceinline__ void load_segment(const InstDesc& d, const TileGeom& 
 // Producer lane j < 19: write segment j of a finished tile back to where it was
 // loaded from, as this lane's bulk async-group.
 template <typename T, bool ODD, int SLOT>
-__device__ __forceinline__ void store_segment(const InstDesc& d, const TileGeom& g, int j, uint32_t buf) {
+__device__ __forceinline__ void store_segment(const SegInst& d, const TileGeom& g, int j, uint32_t buf) {
   const uint32_t row_bytes = (uint32_t)d.nxp * (uint32_t)sizeof(T);
-  const uint32_t seg_bytes = SLOT ? (uint32_t)SLOT : row_bytes * (uint32_t)d.rows;
+  const uint32_t seg_bytes = slotted<SLOT>() ? (uint32_t)SLOT : row_bytes * (uint32_t)d.rows;
   const SegRows sr = seg_rows<T, ODD>(d, g, j);
-  const uint32_t src = buf + (uint32_t)c_gpos[ODD ? c_seg_opp[j] : j] * seg_bytes;  // spos(j, ODD)
+  const uint32_t pos = SLOT == kSlotGrouped ? (uint32_t)c_gpos[ODD ? c_seg_opp[j] : j] : (uint32_t)j;  // spos
+  const uint32_t src = buf + pos * seg_bytes;
   if ((uint32_t)d.row_copy_bytes == row_bytes && sr.step == (int64_t)row_bytes) {
     bulk_store(const_cast<char*>(sr.plane) + (int64_t)sr.ys * row_bytes, src, (uint32_t)sr.first * row_bytes);
     if (sr.first < g.rows)
@@ -302,13 +327,13 @@ __device__ __forceinline__ void store_segment(const InstDesc& d, const TileGeom&
 // rows, each adjacent in global and in shared memory, so producer lane g < 9
 // moves group g in one piece.
 template <typename T, bool ODD, int SLOT>
-__device__ __forceinline__ bool grouped_copies(const InstDesc& d) {
-  return ODD && SLOT == 0 && d.slot_grouped && d.rows == 1 &&
+__device__ __forceinline__ bool grouped_copies(const SegInst& d) {
+  return ODD && SLOT == kSlotGrouped && d.slot_grouped && d.rows == 1 &&
          (uint32_t)d.row_copy_bytes == (uint32_t)d.nxp * (uint32_t)sizeof(T);
 }
 
 template <typename T>
-__device__ __forceinline__ const char* group_src(const InstDesc& d, const TileGeom& g, int k) {
+__device__ __forceinline__ const char* group_src(const SegInst& d, const TileGeom& g, int k) {
   int zs = g.z + c_grp_cz[k];
   zs = zs < 0 ? zs + d.nz : (zs >= d.nz ? zs - d.nz : zs);
   int ys = g.y0 + c_grp_cy[k];
@@ -318,14 +343,14 @@ __device__ __forceinline__ const char* group_src(const InstDesc& d, const TileGe
 }
 
 template <typename T>
-__device__ __forceinline__ void load_group(const InstDesc& d, const TileGeom& g, int k, uint32_t buf, uint32_t bar) {
+__device__ __forceinline__ void load_group(const SegInst& d, const TileGeom& g, int k, uint32_t buf, uint32_t bar) {
   const uint32_t row_bytes = (uint32_t)d.nxp * (uint32_t)sizeof(T);
   bulk_load(buf + (uint32_t)c_grp_start[k] * row_bytes, group_src<T>(d, g, k), (uint32_t)c_grp_len[k] * row_bytes,
             bar);
 }
 
 template <typename T>
-__device__ __forceinline__ void store_group(const InstDesc& d, const TileGeom& g, int k, uint32_t buf) {
+__device__ __forceinline__ void store_group(const SegInst& d, const TileGeom& g, int k, uint32_t buf) {
   const uint32_t row_bytes = (uint32_t)d.nxp * (uint32_t)sizeof(T);
   bulk_store(const_cast<char*>(group_src<T>(d, g, k)), buf + (uint32_t)c_grp_start[k] * row_bytes,
              (uint32_t)c_grp_len[k] * row_bytes);
@@ -335,7 +360,7 @@ __device__ __forceinline__ void store_group(const InstDesc& d, const TileGeom& g
 // Producer lane `lane`: its share of the loads / stores of a tile (a slot
 // group or a segment, or nothing).
 template <typename T, bool ODD, int SLOT>
-__device__ __forceinline__ void tile_load(const InstDesc& d, const TileGeom& g, int lane, uint32_t buf,
+__device__ __forceinline__ void tile_load(const SegInst& d, const TileGeom& g, int lane, uint32_t buf,
                                           uint32_t bar) {
   if (grouped_copies<T, ODD, SLOT>(d)) {
     if (lane < 9) load_group<T>(d, g, lane, buf, bar);
@@ -345,7 +370,7 @@ __device__ __forceinline__ void tile_load(const InstDesc& d, const TileGeom& g, 
 }
 
 template <typename T, bool ODD, int SLOT>
-__device__ __forceinline__ void tile_store(const InstDesc& d, const TileGeom& g, int lane, uint32_t buf) {
+__device__ __forceinline__ void tile_store(const SegInst& d, const TileGeom& g, int lane, uint32_t buf) {
   if (grouped_copies<T, ODD, SLOT>(d)) {
     if (lane < 9) store_group<T>(d, g, lane, buf);
   } else if (lane < 19) {
@@ -354,7 +379,7 @@ __device__ __forceinline__ void tile_store(const InstDesc& d, const TileGeom& g,
 }
 
 // Bytes that the bulk loads of one tile deliver.
-__device__ __forceinline__ uint32_t tile_bytes_of(const InstDesc& d, const TileGeom& g, int esize) {
+__device__ __forceinline__ uint32_t tile_bytes_of(const SegInst& d, const TileGeom& g, int esize) {
   const uint32_t row_bytes = (uint32_t)d.nxp * (uint32_t)esize;
   const uint32_t per_row = (uint32_t)d.row_copy_bytes == row_bytes ? row_bytes : (uint32_t)d.row_copy_bytes;
   return 19u * per_row * (uint32_t)g.rows;
@@ -374,7 +399,7 @@ struct CellLoop {
 // ncell cells in place in shared memory (the AA read and write positions
 // coincide, see the file comment).  fx: Fx(y) from the tile's first row; SMODE:
 // the strain evaluation (lbm_params.strain_mode).
-template <typename T, bool ODD, int MODE, int SMODE>
+template <typename T, bool ODD, int MODE, int SMODE, int SLOT>
 __device__ __forceinline__ void collide_tile(const CellLoop& cl, int ncell, const float* __restrict__ fx,
                                              const float Fy, T* __restrict__ sbuf,
                                              const float* __restrict__ fz_table, int nct, Acc& acc) {
@@ -388,7 +413,7 @@ __device__ __forceinline__ void collide_tile(const CellLoop& cl, int ncell, cons
 #pragma unroll
     for (int a = 0; a < 19; ++a) {
       const int xs = ODD ? (cx(a) > 0 ? xm : (cx(a) < 0 ? xp : x)) : x;
-      f[a] = S::cvt(row[spos(a, ODD) * seg + xs]);
+      f[a] = S::cvt(row[spos<SLOT>(a, ODD) * seg + xs]);
     }
     const float Fx = __ldg(fx + r) + cl.fx_const;
     const float Fz = fz_table[x];
@@ -397,7 +422,7 @@ __device__ __forceinline__ void collide_tile(const CellLoop& cl, int ncell, cons
 #pragma unroll
     for (int a = 0; a < 19; ++a) {
       const int xd = ODD ? (cx(a) > 0 ? xp : (cx(a) < 0 ? xm : x)) : x;
-      row[spos(opp(a), ODD) * seg + xd] = S::pack(f[a]);
+      row[spos<SLOT>(opp(a), ODD) * seg + xd] = S::pack(f[a]);
     }
     if (MODE == MODE_STEP_STATS) acc.add(cd, Fx, Fy, Fz, cl.C);
     x += cl.dx;
@@ -447,10 +472,16 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
     if (ntiles == 0) return;
     TileWalker wl = walker_start(insts, ninst, first, stride);  // next tile to load
     TileWalker ws = wl;                                         // next tile to store
+    SegInst sil = seg_inst(insts[wl.ii]), sis = sil;            // their instances' fields
+    int sil_ii = wl.ii, sis_ii = wl.ii;
     for (; loaded < ntiles && loaded < stages; ++loaded) {
       if (!(withheld && loaded == 0)) {
         const TileGeom g = walker_geom(wl);
-        const InstDesc& d = insts[g.ii];
+        if (g.ii != sil_ii) {
+          sil = seg_inst(insts[g.ii]);
+          sil_ii = g.ii;
+        }
+        const SegInst& d = sil;
         const uint32_t bar = bar_full + 8u * loaded;
         if (lane == 0) mbar_expect_tx(bar, tile_bytes_of(d, g, (int)sizeof(T)));
         __syncwarp();
@@ -476,12 +507,20 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
       }
       const TileGeom g = walker_geom(ws);
       const uint32_t buf = buf0 + (uint32_t)s * tile_bytes;
-      tile_store<T, ODD, SLOT>(insts[g.ii], g, lane, buf);
+      if (g.ii != sis_ii) {
+        sis = seg_inst(insts[g.ii]);
+        sis_ii = g.ii;
+      }
+      tile_store<T, ODD, SLOT>(sis, g, lane, buf);
       walker_next(ws, insts, ninst, stride, tile_hi);
       if (loaded < ntiles) {
         const TileGeom gn = walker_geom(wl);
         walker_next(wl, insts, ninst, stride, tile_hi);
-        const InstDesc& dn = insts[gn.ii];
+        if (gn.ii != sil_ii) {
+          sil = seg_inst(insts[gn.ii]);
+          sil_ii = gn.ii;
+        }
+        const SegInst& dn = sil;
         const uint32_t bar = bar_full + 8u * s;
         if (lane == 0) mbar_expect_tx(bar, tile_bytes_of(dn, gn, (int)sizeof(T)));
         __syncwarp();
@@ -540,7 +579,7 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
       cur = w.ii;
       cl.nx = d.nx;
       cl.nxp = d.nxp;
-      cl.seg = SLOT ? SLOT / (int)sizeof(T) : d.rows * d.nxp;
+      cl.seg = slotted<SLOT>() ? SLOT / (int)sizeof(T) : d.rows * d.nxp;
       cl.dr = nct / d.nx;
       cl.dx = nct - cl.dr * d.nx;
       cl.r0 = ctid / d.nx;
@@ -575,9 +614,9 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
     const int ncell = g.rows * cl.nx;
     T* sbuf = reinterpret_cast<T*>(smem + kBarBytes + (size_t)st * tile_bytes);
     if (smode == 1)
-      collide_tile<T, ODD, MODE, 1>(cl, ncell, fx, Fy, sbuf, fz_table, nct, acc);
+      collide_tile<T, ODD, MODE, 1, SLOT>(cl, ncell, fx, Fy, sbuf, fz_table, nct, acc);
     else
-      collide_tile<T, ODD, MODE, 0>(cl, ncell, fx, Fy, sbuf, fz_table, nct, acc);
+      collide_tile<T, ODD, MODE, 0, SLOT>(cl, ncell, fx, Fy, sbuf, fz_table, nct, acc);
     if (MODE == MODE_STEP_STATS) acc.fold();
     // hand the tile back: make this warp's shared-memory writes visible to the
     // TMA engine, then one arrival per warp
@@ -612,6 +651,7 @@ cudaError_t dispatch_tma(const LaunchArgs& la, cudaStream_t st) {
   if (la.mode == MODE_DIAG) return cudaErrorInvalidValue;
   switch (la.slot_bytes) {
     case 0: return dispatch_tma_s<T, 0>(la, st);
+    case kSlotGrouped: return dispatch_tma_s<T, kSlotGrouped>(la, st);
     case kSlot3: return dispatch_tma_s<T, kSlot3>(la, st);
     case kSlot2: return dispatch_tma_s<T, kSlot2>(la, st);
   }
@@ -634,6 +674,7 @@ cudaError_t set_smem_s(int smem) {
 template <typename T>
 cudaError_t set_smem(int smem) {
   cudaError_t e = set_smem_s<T, 0>(smem);
+  if (e == cudaSuccess) e = set_smem_s<T, kSlotGrouped>(smem);
   if (e == cudaSuccess) e = set_smem_s<T, kSlot3>(smem);
   if (e == cudaSuccess) e = set_smem_s<T, kSlot2>(smem);
   return e;
@@ -645,6 +686,9 @@ cudaError_t occupancy(int* n, int slot_bytes, int threads, int smem_bytes) {
     case 0:
       return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_step_tma<T, true, MODE_STEP_STATS, 0>, threads,
                                                            smem_bytes);
+    case kSlotGrouped:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_step_tma<T, true, MODE_STEP_STATS, kSlotGrouped>,
+                                                           threads, smem_bytes);
     case kSlot3:
       return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_step_tma<T, true, MODE_STEP_STATS, kSlot3>,
                                                            threads, smem_bytes);
