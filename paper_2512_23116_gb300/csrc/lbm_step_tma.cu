@@ -26,7 +26,9 @@
 // cp.async.bulk (the TMA engine; x-lines start on 16-byte boundaries, nxp is
 // padded for that) completing on mbarrier transaction counts, and writes each
 // finished tile back with cp.async.bulk shared->global (its own bulk group, so
-// it reloads its segment as soon as its own store has read it).  Consumers read
+// it reloads its segment as soon as its own store has read it; in the odd steps
+// of one-x-line runtime-stride tiles of the row-interleaved array lane g < 9
+// moves a whole slot group instead, see grouped_copies).  Consumers read
 // the 19 populations of a cell from shared memory, collide in FP32 registers
 // (lbm_device.cuh) and write the 19 results back in place; the populations in
 // global memory are moved by the TMA engine only.  Producer and consumers walk
@@ -461,7 +463,8 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
   __syncthreads();
 
   if (warp == nconsumer_warps) {
-    // ---------------- producer warp: lane j < 19 issues segment j's bulk copies ----------------
+    // ---------------- producer warp: lane j < 19 issues segment j's bulk copies (lane g < 9
+    // slot group g's in the odd steps of grouped runtime-stride tiles) ----------------
     const int64_t first = tile_lo + blockIdx.x;
     const int64_t stride = gridDim.x;
     const int ntiles = first < tile_hi ? (int)((tile_hi - 1 - first) / stride) + 1 : 0;
