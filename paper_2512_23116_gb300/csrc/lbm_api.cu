@@ -462,16 +462,37 @@ int diag_pass(lbm_t h, int i, bool want_u, bool want_aux, int plane_axis, int pl
   la.dout.hist_bins = I.hist_bins;
   la.dout.hist_scale = (float)(I.hist_bins / I.hist_max);
   CK(h, cudaMemsetAsync(h->d_partials, 0, h->partials_elems * sizeof(double), h->stream));
-  // the diagnostic pass always uses the direct kernel: it stores no populations
-  {
+  // The TMA kernel's read-only variant when the handle runs the TMA kernel
+  // (its copy pipeline keeps the loads in flight during the collision
+  // arithmetic; the theta histogram goes behind the Fz table in shared memory
+  // when it fits), else the direct kernel at full occupancy.
+  int grid = 0;
+  if (h->kind == 2) {
+    LaunchArgs lt = la;
+    const int hist_bytes = (I.hist_bins + 1) * 4;
+    const int smem_hist = (h->smem + hist_bytes + 15) / 16 * 16;
+    if (want_hist && smem_hist <= kMaxDynSmem && tma_prepare(h->precision, smem_hist) == cudaSuccess) {
+      lt.hist_smem = h->smem;
+      lt.smem_bytes = smem_hist;
+    }
+    const int bps = tma_max_blocks_per_sm(h->precision, lt.slot_bytes, lt.threads, lt.smem_bytes, true);
+    const int cap = (int)(h->partials_elems / ((size_t)h->inst.size() * kNP));
+    grid = std::min(h->num_sms * bps, cap);
+    if (grid > 0) {
+      lt.grid = grid;
+      lt.sa.grid = grid;
+      CK(h, launch_step_tma(lt, h->stream));
+    }
+  }
+  if (grid == 0) {
     LaunchArgs ld = la;
     ld.threads = 256;
-    ld.grid = diag_grid(h);
+    ld.grid = grid = diag_grid(h);
     ld.sa.grid = ld.grid;
     CK(h, launch_step_direct(ld, h->stream));
   }
-  CK(h, launch_finish(h->d_partials, (int)h->inst.size(), diag_grid(h), h->d_results, nullptr, nullptr,
-                      0, h->d_err, h->stream));
+  CK(h, launch_finish(h->d_partials, (int)h->inst.size(), grid, h->d_results, nullptr, nullptr, 0, h->d_err,
+                      h->stream));
   return LBM_OK;
 }
 

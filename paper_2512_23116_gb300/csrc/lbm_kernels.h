@@ -28,6 +28,8 @@ struct LaunchArgs {
   uint32_t* err;           // device error word
   long long wait_ns;       // bound of every device-side wait (nanoseconds)
   int withhold_first_load; // test hook: block 0 never loads its first tile
+  int hist_smem;           // TMA statistics pass: byte offset of the theta histogram in
+                           // dynamic shared memory (0: global counts)
 };
 
 cudaError_t launch_step_direct(const LaunchArgs& la, cudaStream_t st);
@@ -45,10 +47,14 @@ constexpr int kSlot2 = 5760;
 constexpr int kSlotGrouped = -1;
 
 cudaError_t launch_step_tma(const LaunchArgs& la, cudaStream_t st);
+// Dynamic shared memory a block may request (227 KB on sm_100 / sm_103).
+constexpr int kMaxDynSmem = 232448;
 // Dynamic shared memory of the TMA kernel: barriers, `stages` tile buffers and
 // the Fz(x) table of the widest instance.
 int tma_smem_bytes(int stages, int tile_bytes, int max_nx);
-int tma_max_blocks_per_sm(int precision, int slot_bytes, int threads, int smem_bytes);
+// Resident blocks per SM of the step variants (diag = false) or of the
+// read-only statistics pass (diag = true).
+int tma_max_blocks_per_sm(int precision, int slot_bytes, int threads, int smem_bytes, bool diag = false);
 cudaError_t tma_prepare(int precision, int smem_bytes);
 
 // Initial condition: f' = equilibrium of (drho, u), written at AA parity `odd`,

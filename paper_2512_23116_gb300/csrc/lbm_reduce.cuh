@@ -12,14 +12,21 @@
 
 namespace lbm {
 
-// Per-thread accumulation: the few cells a thread updates in one tile are
-// summed in FP32 (`t`), and each tile's sums are added to the FP64 totals
-// (`s`) by fold(); the block and grid reductions are FP64.
+// Cells a thread sums in FP32 before it adds the sums to its FP64 totals:
+// FP64 arithmetic is slow on this part (a fold per tile of one x-line cost ~9
+// FP64 operations per cell, a quarter of the statistics pass at 800^3), and
+// an FP32 sum of 32 terms is exact to ~32 x 2^-24 of its magnitude.
+constexpr uint32_t kFoldCells = 32;
+
+// Per-thread accumulation: the cells a thread updates are summed in FP32 (`t`)
+// and added to the FP64 totals (`s`) by fold(), at the end of a tile once at
+// least kFoldCells cells have been summed (fold_if_full); the block and grid
+// reductions are FP64.
 struct Acc {
   double s[kNSum];
   float t[kNSum];
   float thmin, thmax;
-  uint32_t bad, cells;
+  uint32_t bad, cells, tn;
 
   __device__ __forceinline__ void reset() {
 #pragma unroll
@@ -31,6 +38,7 @@ struct Acc {
     thmax = -FLT_MAX;
     bad = 0;
     cells = 0;
+    tn = 0;
   }
 
   // Energy E_k = <u.u>/2, injection <F.u>, dissipation 2 nu <S_ij S_ij> with
@@ -61,16 +69,55 @@ struct Acc {
     const float chk = g.drho + g.ux + g.uy + g.uz + g.snorm;
     bad += isfinite(chk) ? 0u : 1u;
     cells += 1u;
+    tn += 1u;
   }
 
-  // Move the FP32 tile sums into the FP64 totals.
+  // Move the FP32 sums into the FP64 totals.
   __device__ __forceinline__ void fold() {
 #pragma unroll
     for (int k = 0; k < kNSum; ++k) {
       s[k] += (double)t[k];
       t[k] = 0.f;
     }
+    tn = 0;
   }
+
+  __device__ __forceinline__ void fold_if_full() {
+    if (tn >= kFoldCells) fold();
+  }
+};
+
+// A thread's run of cells in one theta-histogram bin: the count goes to the
+// histogram (one atomic add) when the bin changes and at the end.  Theta
+// concentrates in a few bins, so per-cell increments, even warp-aggregated
+// ones, would serialise on the same words.  Counts in global memory (a
+// histogram too large for the block's shared memory) are also summed over the
+// warp's lanes that flush the same bin: contended atomics in L2 cost far more
+// than the match; in shared memory they do not.
+struct HistRun {
+  int bin = -1;
+  uint32_t n = 0;
+
+  // Called by every active lane; lanes with `go` add their run.
+  __device__ __forceinline__ void flush_if(uint32_t* hist, bool go, bool global) {
+    go = go && n > 0;
+    if (!global) {
+      if (go) {
+        atomicAdd(&hist[bin], n);
+        n = 0;
+      }
+      return;
+    }
+    const unsigned fl = __ballot_sync(__activemask(), go);
+    if (go) {
+      const unsigned grp = __match_any_sync(fl, bin);
+      const unsigned tot = __reduce_add_sync(grp, n);
+      if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&hist[bin], tot);
+      n = 0;
+    }
+  }
+
+  __device__ __forceinline__ void flush(uint32_t* hist, bool global) { flush_if(hist, true, global); }
 };
 
 // Reduce the accumulators of the `nthreads` threads that call this (a whole
@@ -123,9 +170,12 @@ static __device__ __noinline__ void block_flush(Acc& acc, double* __restrict__ d
   named_sync(bar_id, nthreads);
 }
 
-// Per-cell outputs of the read-only diagnostic pass.
+// Per-cell outputs of the read-only diagnostic pass; `hist` (shared-memory
+// counts, or global ones when hist_global, or null) receives the thread's
+// histogram runs.
 __device__ __forceinline__ void diag_write(const DiagOut& o, const CellDiag& g, int x, int y, int z,
-                                           int nx, int ny, int nz, uint32_t* shist) {
+                                           int nx, int ny, int nz, uint32_t* hist, bool hist_global,
+                                           HistRun& run) {
   const int64_t n = (int64_t)nx * ny * nz;
   const int64_t i = ((int64_t)z * ny + y) * nx + x;
   if (o.u) {
@@ -143,13 +193,14 @@ __device__ __forceinline__ void diag_write(const DiagOut& o, const CellDiag& g, 
     if (o.plane_axis == 1 && y == o.plane_index) o.plane[(int64_t)z * nx + x] = g.theta;
     if (o.plane_axis == 2 && z == o.plane_index) o.plane[(int64_t)y * nx + x] = g.theta;
   }
-  if (shist) {
+  if (hist) {
     int b = o.hist_bins;
     const float q = g.theta * o.hist_scale;
     if (q >= 0.f && q < (float)o.hist_bins) b = min((int)q, o.hist_bins - 1);
-    // lanes that fall into the same bin add once (theta is often uniform)
-    const unsigned same = __match_any_sync(__activemask(), b);
-    if ((threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&shist[b], (uint32_t)__popc(same));
+    const bool change = b != run.bin;
+    run.flush_if(hist, change, hist_global);
+    if (change) run.bin = b;
+    run.n += 1u;
   }
 }
 

@@ -31,6 +31,8 @@ k_step_direct(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, in
   }
   Acc acc;
   acc.reset();
+  HistRun run;
+  uint32_t* const hist = use_hist ? shist : dout.hist;
   int cur = -1, hint = 0;
   for (int64_t t = tile_lo + blockIdx.x; t < tile_hi; t += gridDim.x) {
     const int ii = find_instance(insts, ninst, t, cur < 0 ? hint : cur);
@@ -97,7 +99,7 @@ k_step_direct(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, in
         }
       }
       if (MODE != MODE_STEP) acc.add(g, Fx, Fy, Fz, C);
-      if (MODE == MODE_DIAG) diag_write(dout, g, x, y, z, nx, ny, nz, use_hist ? shist : dout.hist);
+      if (MODE == MODE_DIAG) diag_write(dout, g, x, y, z, nx, ny, nz, hist, !use_hist, run);
       x += dx;
       r += dr;
       if (x >= nx) {
@@ -105,12 +107,13 @@ k_step_direct(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, in
         r += 1;
       }
     }
-    if (MODE != MODE_STEP) acc.fold();
+    if (MODE != MODE_STEP) acc.fold_if_full();
   }
   if (MODE != MODE_STEP) {
     if (cur >= 0)
       block_flush(acc, sa.partials + ((int64_t)cur * sa.grid + blockIdx.x) * kNP, blockDim.x, 0);
   }
+  if (MODE == MODE_DIAG && hist) run.flush(hist, !use_hist);
   if (use_hist) {
     __syncthreads();
     for (int i = threadIdx.x; i <= dout.hist_bins; i += blockDim.x)

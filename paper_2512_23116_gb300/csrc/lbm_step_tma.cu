@@ -36,6 +36,12 @@
 // wait is bounded by the global timer: on expiry the block records
 // ERR_TIMEOUT, stops issuing, waits (bounded) for its loads in flight and for
 // its stores, and returns.
+//
+// MODE_DIAG is the read-only statistics pass over the current state: the same
+// loads and collision arithmetic, no stores (a stage is reloaded as soon as
+// its consumers are done), the FP64 block partials of the step with
+// statistics, and the per-cell outputs (velocity, theta slices, theta
+// histogram in shared memory when the launch reserves room for it).
 #include <cuda_runtime.h>
 
 #include "lbm_device.cuh"
@@ -397,14 +403,26 @@ struct CellLoop {
   float nu0, s_nu0, C;
 };
 
+// Per-cell outputs of the read-only statistics pass (MODE_DIAG) for a tile:
+// the outputs, the tile's first row and plane, the extents, the histogram
+// (shared memory or global counts).
+struct DiagTile {
+  DiagOut o;
+  int y0, z, ny, nz;
+  uint32_t* hist;
+  bool hist_global;
+};
+
 // Consumer thread of nct: collide cells r0 nx + x0, + nct, ... of a tile of
 // ncell cells in place in shared memory (the AA read and write positions
 // coincide, see the file comment).  fx: Fx(y) from the tile's first row; SMODE:
-// the strain evaluation (lbm_params.strain_mode).
+// the strain evaluation (lbm_params.strain_mode).  MODE_DIAG leaves the tile
+// unchanged and writes the per-cell outputs instead.
 template <typename T, bool ODD, int MODE, int SMODE, int SLOT>
 __device__ __forceinline__ void collide_tile(const CellLoop& cl, int ncell, const float* __restrict__ fx,
                                              const float Fy, T* __restrict__ sbuf,
-                                             const float* __restrict__ fz_table, int nct, Acc& acc) {
+                                             const float* __restrict__ fz_table, int nct, Acc& acc,
+                                             const DiagTile& dt, HistRun& run) {
   using S = Storage<T>;
   const int nx = cl.nx, seg = cl.seg;
   int r = cl.r0, x = cl.x0;
@@ -421,12 +439,15 @@ __device__ __forceinline__ void collide_tile(const CellLoop& cl, int ncell, cons
     const float Fz = fz_table[x];
     CellDiag cd;
     mrt_collide(f, Fx, Fy, Fz, cl.nu0, cl.s_nu0, cl.C, cd, SMODE);
+    if (MODE != MODE_DIAG) {
 #pragma unroll
-    for (int a = 0; a < 19; ++a) {
-      const int xd = ODD ? (cx(a) > 0 ? xp : (cx(a) < 0 ? xm : x)) : x;
-      row[spos<SLOT>(opp(a), ODD) * seg + xd] = S::pack(f[a]);
+      for (int a = 0; a < 19; ++a) {
+        const int xd = ODD ? (cx(a) > 0 ? xp : (cx(a) < 0 ? xm : x)) : x;
+        row[spos<SLOT>(opp(a), ODD) * seg + xd] = S::pack(f[a]);
+      }
     }
-    if (MODE == MODE_STEP_STATS) acc.add(cd, Fx, Fy, Fz, cl.C);
+    if (MODE != MODE_STEP) acc.add(cd, Fx, Fy, Fz, cl.C);
+    if (MODE == MODE_DIAG) diag_write(dt.o, cd, x, dt.y0 + r, dt.z, nx, dt.ny, dt.nz, dt.hist, dt.hist_global, run);
     x += cl.dx;
     r += cl.dr;
     if (x >= nx) {
@@ -440,7 +461,7 @@ template <typename T, bool ODD, int MODE, int SLOT>
 __global__ void __launch_bounds__(512, 1)
 k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64_t tile_hi,
            StatsArgs sa, int stages, int tile_bytes, uint32_t* __restrict__ err, long long wait_ns,
-           int withhold_first_load) {
+           int withhold_first_load, DiagOut dout, int hist_smem) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nconsumer_warps = (blockDim.x >> 5) - 1;
@@ -514,7 +535,7 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
         sis = seg_inst(insts[g.ii]);
         sis_ii = g.ii;
       }
-      tile_store<T, ODD, SLOT>(sis, g, lane, buf);
+      if (MODE != MODE_DIAG) tile_store<T, ODD, SLOT>(sis, g, lane, buf);
       walker_next(ws, insts, ninst, stride, tile_hi);
       if (loaded < ntiles) {
         const TileGeom gn = walker_geom(wl);
@@ -557,8 +578,17 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
   const int64_t first = tile_lo + blockIdx.x;
   const int64_t stride = gridDim.x;
   if (first >= tile_hi) return;
+  // MODE_DIAG: theta histogram in shared memory when the launch reserved room
+  // at byte hist_smem, else straight into the global counts
+  uint32_t* hist = nullptr;
+  if (MODE == MODE_DIAG && dout.hist) {
+    hist = hist_smem > 0 ? reinterpret_cast<uint32_t*>(smem + hist_smem) : dout.hist;
+    if (hist_smem > 0)
+      for (int i = ctid; i <= dout.hist_bins; i += nct) hist[i] = 0u;
+  }
   Acc acc;
   acc.reset();
+  HistRun run;
   int cur = -1;
   bool ok = true;
   CellLoop cl{};
@@ -572,7 +602,7 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
     if (w.ii != cur) {
       // new instance: flush its predecessor's statistics, reload Fz(x) and the
       // per-instance constants
-      if (MODE == MODE_STEP_STATS && cur >= 0)
+      if (MODE != MODE_STEP && cur >= 0)
         block_flush(acc, sa.partials + ((int64_t)cur * sa.grid + blockIdx.x) * kNP, nct, 1);
       acc.reset();
       const InstDesc& d = insts[w.ii];
@@ -616,19 +646,26 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
     const float Fy = __ldg(fy_of_z + g.z) + fy_const;
     const int ncell = g.rows * cl.nx;
     T* sbuf = reinterpret_cast<T*>(smem + kBarBytes + (size_t)st * tile_bytes);
+    const DiagTile dt{dout, g.y0, g.z, insts[w.ii].ny, insts[w.ii].nz, hist, hist_smem == 0};
     if (smode == 1)
-      collide_tile<T, ODD, MODE, 1, SLOT>(cl, ncell, fx, Fy, sbuf, fz_table, nct, acc);
+      collide_tile<T, ODD, MODE, 1, SLOT>(cl, ncell, fx, Fy, sbuf, fz_table, nct, acc, dt, run);
     else
-      collide_tile<T, ODD, MODE, 0, SLOT>(cl, ncell, fx, Fy, sbuf, fz_table, nct, acc);
-    if (MODE == MODE_STEP_STATS) acc.fold();
+      collide_tile<T, ODD, MODE, 0, SLOT>(cl, ncell, fx, Fy, sbuf, fz_table, nct, acc, dt, run);
+    if (MODE != MODE_STEP) acc.fold_if_full();
     // hand the tile back: make this warp's shared-memory writes visible to the
     // TMA engine, then one arrival per warp
     fence_async_smem();
     __syncwarp();
     if (lane == 0) mbar_arrive(bar_done + 8u * st);
   }
-  if (MODE == MODE_STEP_STATS && cur >= 0)
+  if (MODE != MODE_STEP && cur >= 0)
     block_flush(acc, sa.partials + ((int64_t)cur * sa.grid + blockIdx.x) * kNP, nct, 1);
+  if (MODE == MODE_DIAG && hist) run.flush(hist, hist_smem == 0);
+  if (MODE == MODE_DIAG && dout.hist && hist_smem > 0) {
+    named_sync(2, nct);
+    for (int i = ctid; i <= dout.hist_bins; i += nct)
+      if (hist[i]) atomicAdd(&dout.hist[i], hist[i]);
+  }
 }
 
 template <typename T, bool ODD, int MODE, int SLOT>
@@ -636,22 +673,24 @@ cudaError_t launch_tma_t(const LaunchArgs& la, cudaStream_t st) {
   (void)cudaGetLastError();  // errors of earlier calls were reported by their return codes
   k_step_tma<T, ODD, MODE, SLOT><<<la.grid, la.threads, la.smem_bytes, st>>>(
       la.insts, la.ninst, la.tile_lo, la.tile_hi, la.sa, la.stages, la.tile_bytes_max, la.err,
-      la.wait_ns, la.withhold_first_load);
+      la.wait_ns, la.withhold_first_load, la.dout, la.hist_smem);
   return cudaGetLastError();
 }
 
 template <typename T, int SLOT>
 cudaError_t dispatch_tma_s(const LaunchArgs& la, cudaStream_t st) {
-  if (la.odd)
-    return la.mode == MODE_STEP ? launch_tma_t<T, true, MODE_STEP, SLOT>(la, st)
-                                : launch_tma_t<T, true, MODE_STEP_STATS, SLOT>(la, st);
-  return la.mode == MODE_STEP ? launch_tma_t<T, false, MODE_STEP, SLOT>(la, st)
-                              : launch_tma_t<T, false, MODE_STEP_STATS, SLOT>(la, st);
+  if (la.odd) {
+    if (la.mode == MODE_STEP) return launch_tma_t<T, true, MODE_STEP, SLOT>(la, st);
+    if (la.mode == MODE_STEP_STATS) return launch_tma_t<T, true, MODE_STEP_STATS, SLOT>(la, st);
+    return launch_tma_t<T, true, MODE_DIAG, SLOT>(la, st);
+  }
+  if (la.mode == MODE_STEP) return launch_tma_t<T, false, MODE_STEP, SLOT>(la, st);
+  if (la.mode == MODE_STEP_STATS) return launch_tma_t<T, false, MODE_STEP_STATS, SLOT>(la, st);
+  return launch_tma_t<T, false, MODE_DIAG, SLOT>(la, st);
 }
 
 template <typename T>
 cudaError_t dispatch_tma(const LaunchArgs& la, cudaStream_t st) {
-  if (la.mode == MODE_DIAG) return cudaErrorInvalidValue;
   switch (la.slot_bytes) {
     case 0: return dispatch_tma_s<T, 0>(la, st);
     case kSlotGrouped: return dispatch_tma_s<T, kSlotGrouped>(la, st);
@@ -666,7 +705,9 @@ cudaError_t set_smem_s(int smem) {
   const void* fns[] = {(const void*)k_step_tma<T, false, MODE_STEP, SLOT>,
                        (const void*)k_step_tma<T, true, MODE_STEP, SLOT>,
                        (const void*)k_step_tma<T, false, MODE_STEP_STATS, SLOT>,
-                       (const void*)k_step_tma<T, true, MODE_STEP_STATS, SLOT>};
+                       (const void*)k_step_tma<T, true, MODE_STEP_STATS, SLOT>,
+                       (const void*)k_step_tma<T, false, MODE_DIAG, SLOT>,
+                       (const void*)k_step_tma<T, true, MODE_DIAG, SLOT>};
   for (const void* f : fns) {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
@@ -683,21 +724,20 @@ cudaError_t set_smem(int smem) {
   return e;
 }
 
-template <typename T>
+template <typename T, int MODE>
 cudaError_t occupancy(int* n, int slot_bytes, int threads, int smem_bytes) {
   switch (slot_bytes) {
     case 0:
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_step_tma<T, true, MODE_STEP_STATS, 0>, threads,
-                                                           smem_bytes);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_step_tma<T, true, MODE, 0>, threads, smem_bytes);
     case kSlotGrouped:
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_step_tma<T, true, MODE_STEP_STATS, kSlotGrouped>,
-                                                           threads, smem_bytes);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_step_tma<T, true, MODE, kSlotGrouped>, threads,
+                                                           smem_bytes);
     case kSlot3:
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_step_tma<T, true, MODE_STEP_STATS, kSlot3>,
-                                                           threads, smem_bytes);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_step_tma<T, true, MODE, kSlot3>, threads,
+                                                           smem_bytes);
     case kSlot2:
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_step_tma<T, true, MODE_STEP_STATS, kSlot2>,
-                                                           threads, smem_bytes);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_step_tma<T, true, MODE, kSlot2>, threads,
+                                                           smem_bytes);
   }
   return cudaErrorInvalidValue;
 }
@@ -736,13 +776,22 @@ cudaError_t tma_prepare(int precision, int smem_bytes) {
   return e;
 }
 
-int tma_max_blocks_per_sm(int precision, int slot_bytes, int threads, int smem_bytes) {
+int tma_max_blocks_per_sm(int precision, int slot_bytes, int threads, int smem_bytes, bool diag) {
   int n = 0;
   cudaError_t e = cudaErrorInvalidValue;
   switch (precision) {
-    case 0: e = occupancy<float>(&n, slot_bytes, threads, smem_bytes); break;
-    case 1: e = occupancy<__half>(&n, slot_bytes, threads, smem_bytes); break;
-    case 2: e = occupancy<__nv_bfloat16>(&n, slot_bytes, threads, smem_bytes); break;
+    case 0:
+      e = diag ? occupancy<float, MODE_DIAG>(&n, slot_bytes, threads, smem_bytes)
+               : occupancy<float, MODE_STEP_STATS>(&n, slot_bytes, threads, smem_bytes);
+      break;
+    case 1:
+      e = diag ? occupancy<__half, MODE_DIAG>(&n, slot_bytes, threads, smem_bytes)
+               : occupancy<__half, MODE_STEP_STATS>(&n, slot_bytes, threads, smem_bytes);
+      break;
+    case 2:
+      e = diag ? occupancy<__nv_bfloat16, MODE_DIAG>(&n, slot_bytes, threads, smem_bytes)
+               : occupancy<__nv_bfloat16, MODE_STEP_STATS>(&n, slot_bytes, threads, smem_bytes);
+      break;
   }
   return e == cudaSuccess ? n : 0;
 }
