@@ -475,6 +475,14 @@ int diag_pass(lbm_t h, int i, bool want_u, bool want_aux, int plane_axis, int pl
       lt.hist_smem = h->smem;
       lt.smem_bytes = smem_hist;
     }
+    // the pass is bound by its consumers' arithmetic, not by the copies: as
+    // many consumer warps as fit (the tiles do not depend on the thread count)
+    for (int th : {512, 384, h->threads}) {
+      if (tma_max_blocks_per_sm(h->precision, lt.slot_bytes, th, lt.smem_bytes, true) >= 1) {
+        lt.threads = th;
+        break;
+      }
+    }
     const int bps = tma_max_blocks_per_sm(h->precision, lt.slot_bytes, lt.threads, lt.smem_bytes, true);
     const int cap = (int)(h->partials_elems / ((size_t)h->inst.size() * kNP));
     grid = std::min(h->num_sms * bps, cap);
