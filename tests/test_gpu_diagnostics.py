@@ -80,21 +80,49 @@ def test_domain_stats_match_oracle(gpu_lib):
         assert math.isclose(st[k], iso[kk], rel_tol=1e-3, abs_tol=1e-7), (k, st[k], iso[kk])
 
 
-def test_histogram_counts(gpu_lib):
+# (kernel configuration, bins): the statistics pass of the direct kernel keeps
+# up to 12000 bins in shared memory, global counts above; the TMA kernel's
+# keeps them in shared memory behind its stages when they fit (runtime-stride
+# tiles of two 16-cell x-lines: 2.4 KB stages) and uses global counts summed
+# over the warp's lanes that flush the same bin when they do not (5760 B
+# slots: 214 KB of stages; or 60000 bins)
+HIST_PATHS = [
+    (dict(kernel=1, tile_rows=2, threads=256), 4096),
+    (dict(kernel=1, tile_rows=2, threads=256), 20000),
+    (dict(kernel=2, tile_rows=2, stages=2, threads=256, tma_slots=1), 4096),
+    (dict(kernel=2, tile_rows=2, stages=2, threads=256), 4096),
+    (dict(kernel=2, tile_rows=2, stages=2, threads=256, tma_slots=1), 60000),
+]
+
+
+@pytest.mark.parametrize("steps", [10, 11])
+@pytest.mark.parametrize("cfg,bins", HIST_PATHS)
+def test_histogram_counts(gpu_lib, cfg, bins, steps):
+    """Every histogram path of the statistics pass, at both AA parities: the
+    counts are exactly those of the pass's own per-cell theta (a per-thread
+    run of cells in one bin is added when the bin changes, so no cell may be
+    lost or counted twice)."""
     lbm = gpu_lib
-    gpu, ref, nu0 = _les_case(lbm, n=16, steps=10)
-    with gpu:
-        gpu.step(10)
-        gpu.stats()
-        h = lbm.lbm_histogram(gpu.h, 0, 4096)
-        th = gpu.fields()["theta"]
-    assert int(h.sum()) == 16 ** 3
+    n = 16
+    u = synthetic.random_solenoidal(n, seed=1, urms=0.05)
+    nu0 = oracle.derive_nu0(0.043, n, 2e3)
+    F0 = oracle.forcing_amplitude(0.2, 0.043, n)
+    p = lbm.make_params(n, nu0=nu0, cs=0.13, f0=F0, force_mode=lbm.LBM_FORCE_PAPER_SIN, hist_bins=bins,
+                        hist_max=0.02, **cfg)
+    with lbm.Lattice(p) as L:
+        assert L.config()["kind"] == cfg["kernel"]
+        L.init(lbm.LBM_INIT_VELOCITY, u=u)
+        L.step(steps)
+        L.stats()
+        h = lbm.lbm_histogram(L.h, 0, bins)
+        th = L.fields()["theta"]
+    assert int(h.sum()) == n ** 3
     # bin = floor(theta * bins / hist_max) in FP32; theta >= hist_max -> overflow bin
-    q = th.astype(np.float32) * np.float32(4096 / 0.02)
-    idx = np.where(q < 4096, np.floor(q), 4096).astype(np.int64)
-    want = np.bincount(idx.ravel(), minlength=4097)
+    q = th.astype(np.float32) * np.float32(bins / 0.02)
+    idx = np.where(q < bins, np.floor(q), bins).astype(np.int64)
+    want = np.bincount(idx.ravel(), minlength=bins + 1)
     assert np.array_equal(h, want)
-    assert h[4096] > 0  # this LES case has theta above 0.02 somewhere
+    assert np.count_nonzero(h[:bins]) > 10  # theta spread over many bins
 
 
 def test_spectrum_single_mode(gpu_lib):
