@@ -44,6 +44,11 @@ def dist_env():
     return world, rank, local
 
 
+# Nominal HBM3e bandwidth of one GB300 (~8 TB/s), the second denominator the
+# roofline fractions are quoted against beside the measured copy bandwidth.
+NOMINAL_HBM_GBS = 8000.0
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -471,7 +476,7 @@ def sweep(lbm, device, stream, sizes=(128, 256, 512, 1024), steps=500, warmup=5,
             gbs = n ** 3 * BYTES_PER_UPDATE[prec] * steps / (ms * 1e-3) / 1e9
             rows.append({"N": n, "storage": ["fp32", "fp16_shifted"][prec], "steps": steps,
                          "MLUPS": n ** 3 * steps / (ms * 1e-3) / 1e6, "GB_s": gbs, "frac_hbm": gbs / hbm_peak,
-                         "kernel": cfg})
+                         "frac_of_nominal": gbs / NOMINAL_HBM_GBS, "kernel": cfg})
         del u
         torch.cuda.empty_cache()
     n = 128
@@ -659,6 +664,7 @@ def main():
     tpu = traffic_per_update(digest)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "peak_kind": peak_kind,
+                "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "nominal_gbs": NOMINAL_HBM_GBS,
                 "traffic": None if tpu is None else tpu * cells,
                 "algorithmic_bytes_per_launch": cells * BYTES_PER_UPDATE[0]}
 
@@ -672,6 +678,8 @@ def main():
                 "MLUPS": cells * args.steps / (ms2 * 1e-3) / 1e6, "ms_per_step": ms2 / args.steps,
                 "GB_s": cells * BYTES_PER_UPDATE[prec] * args.steps / (ms2 * 1e-3) / 1e9,
                 "frac_hbm": cells * BYTES_PER_UPDATE[prec] * args.steps / (ms2 * 1e-3) / 1e9 / hbm_peak,
+                "frac_of_nominal": cells * BYTES_PER_UPDATE[prec] * args.steps / (ms2 * 1e-3) / 1e9
+                / NOMINAL_HBM_GBS,
                 "speedup_vs_fp32": ms / ms2, "kernel": cfg2}
             if prec == 1:
                 extra[f"{n}^3_{name}"]["dram_bytes_per_update"] = traffic_per_update(digest, "fp16")
