@@ -43,27 +43,31 @@ struct Acc {
 
   // Energy E_k = <u.u>/2, injection <F.u>, dissipation 2 nu <S_ij S_ij> with
   // S_ij S_ij = |S|^2/2 (Eqs. energy_balance, strain_norm), theta = tau_e - 1/2.
+  // Every rounding is spelled out (fused multiply-adds as __fmaf_rn): left to
+  // the compiler, the contraction of these sums into FMAs differed between the
+  // kernel variants, and equal per-cell values must give equal statistics in
+  // every tile layout and kernel configuration.
   __device__ __forceinline__ void add(const CellDiag& g, float Fx, float Fy, float Fz, float C) {
-    const float rho = 1.f + g.drho;
+    const float rho = __fadd_rn(1.f, g.drho);
     const float ux = g.ux, uy = g.uy, uz = g.uz;
     const float sn = g.snorm, th = g.theta;
-    const float ss = sn * sn;
-    t[P_DRHO] += g.drho;
-    t[P_MX] += rho * ux;
-    t[P_MY] += rho * uy;
-    t[P_MZ] += rho * uz;
-    t[P_UU] += ux * ux + uy * uy + uz * uz;
-    t[P_FU] += Fx * ux + Fy * uy + Fz * uz;
-    t[P_SS] += ss;
-    t[P_NUTSS] += C * sn * ss;
-    t[P_TH] += th;
-    t[P_TH2] += th * th;
-    t[P_XX] += ux * ux;
-    t[P_YY] += uy * uy;
-    t[P_ZZ] += uz * uz;
-    t[P_XY] += ux * uy;
-    t[P_XZ] += ux * uz;
-    t[P_YZ] += uy * uz;
+    const float ss = __fmul_rn(sn, sn);
+    t[P_DRHO] = __fadd_rn(t[P_DRHO], g.drho);
+    t[P_MX] = __fmaf_rn(rho, ux, t[P_MX]);
+    t[P_MY] = __fmaf_rn(rho, uy, t[P_MY]);
+    t[P_MZ] = __fmaf_rn(rho, uz, t[P_MZ]);
+    t[P_UU] = __fadd_rn(t[P_UU], __fmaf_rn(ux, ux, __fmaf_rn(uy, uy, __fmul_rn(uz, uz))));
+    t[P_FU] = __fadd_rn(t[P_FU], __fmaf_rn(Fx, ux, __fmaf_rn(Fy, uy, __fmul_rn(Fz, uz))));
+    t[P_SS] = __fadd_rn(t[P_SS], ss);
+    t[P_NUTSS] = __fmaf_rn(__fmul_rn(C, sn), ss, t[P_NUTSS]);
+    t[P_TH] = __fadd_rn(t[P_TH], th);
+    t[P_TH2] = __fmaf_rn(th, th, t[P_TH2]);
+    t[P_XX] = __fmaf_rn(ux, ux, t[P_XX]);
+    t[P_YY] = __fmaf_rn(uy, uy, t[P_YY]);
+    t[P_ZZ] = __fmaf_rn(uz, uz, t[P_ZZ]);
+    t[P_XY] = __fmaf_rn(ux, uy, t[P_XY]);
+    t[P_XZ] = __fmaf_rn(ux, uz, t[P_XZ]);
+    t[P_YZ] = __fmaf_rn(uy, uz, t[P_YZ]);
     thmin = fminf(thmin, g.theta);
     thmax = fmaxf(thmax, g.theta);
     const float chk = g.drho + g.ux + g.uy + g.uz + g.snorm;
@@ -128,7 +132,7 @@ __device__ __forceinline__ void named_sync(int bar_id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(nthreads) : "memory");
 }
 
-static __device__ __noinline__ void block_flush(Acc& acc, double* __restrict__ dst, int nthreads,
+static __device__ __forceinline__ void block_flush(Acc& acc, double* __restrict__ dst, int nthreads,
                                          int bar_id) {
   __shared__ double red[32][kNP];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
