@@ -231,7 +231,8 @@ int64_t lbm_time(lbm_t h);
 /* Statistics of instance `inst` at the current time: one read-only pass of the
  * step kernel computes the same per-cell quantities as a collision (drho, u, |S|,
  * theta) and reduces them in FP64; `what` adds LBM_STATS_SPECTRUM and/or
- * LBM_STATS_STRUCTURE.  Synchronous.  Errors: INVALID_ARG, UNSTABLE, CUDA. */
+ * LBM_STATS_STRUCTURE.  Synchronous.  Errors: INVALID_ARG, UNSTABLE, TIMEOUT
+ * (a bounded wait of the TMA kernel's pass gave up), CUDA. */
 int lbm_stats(lbm_t h, int32_t inst, int32_t what, lbm_stats_t* out);
 
 /* Fused in-step records (params.stats_every > 0) of instance `inst` appended
