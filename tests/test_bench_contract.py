@@ -39,3 +39,35 @@ def test_traffic_figure_matches_its_digest():
     assert bench.traffic_per_update(digest) == float(vals["dram_bytes_per_update_fp32"])
     assert bench.traffic_per_update(digest, "fp16") == float(vals["dram_bytes_per_update_fp16"])
     assert bench.traffic_per_update("0" * 16) is None
+
+
+def _run_bench(args, env_extra=None):
+    import json
+    import subprocess
+    import sys
+    env = dict(os.environ)
+    env.update(env_extra or {})
+    out = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), *args], capture_output=True,
+                         text=True, env=env, cwd=bench.ROOT, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    return [json.loads(ln) for ln in lines]
+
+
+def test_reference_arm_line():
+    """The reference arm (the FP64 oracle on the host cores, no GPU) prints the
+    contract's JSON line: one line, its own metric and config, a cpu_baseline
+    that describes the run and an e2e with no host-device bytes."""
+    (line,) = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "3"])
+    assert line["impl"] == "reference" and line["unit"] == "MLUPS" and line["value"] > 0
+    assert line["higher_is_better"] is True and line["steps"] == 1 and line["warmup"] == 3
+    assert line["dtype"] == "f64" and line["data"] == "synthetic" and "workload" in line["config"]
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1 and cb["sample"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_reference_arm_other_ranks_print_nothing():
+    assert _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "3"], {"RANK": "1", "WORLD_SIZE": "2"}) == []
