@@ -264,3 +264,34 @@ def test_single_cell_collision_matches_the_lattice_step():
             xd, yd, zd = (x + c[a][0]) % 5, (y + c[a][1]) % 4, (z + c[a][2]) % 3
             assert g[a, zd, yd, xd] == fs[a]
         assert th >= 3 * 0.004
+
+
+def test_paper_forcing_is_a_solenoidal_large_scale_field():
+    """Eq. (forcing_pattern) with the amplitude of Eq. (forcing_amplitude): each
+    component is a single Fourier mode of the box (|k| = 2 pi / N) along a
+    coordinate other than its own, so the force is divergence-free, sums to
+    zero over the box, and has mean square F0^2 / 2 per component and peak
+    value F0 (N divisible by 4).  A component tied to its own coordinate, a
+    wrong wave number or a lost component fails here."""
+    n, F0 = 8, 1e-3
+    L = oracle.OracleLBM(n, n, n, 0.01, 0.0, oracle.FORCE_PAPER_SIN, F0=F0)
+    F = L.force_field()  # [3][z][y][x], components (x, y, z)
+    Fh = np.fft.fftn(F, axes=(1, 2, 3))
+    k = np.rint(np.fft.fftfreq(n) * n).astype(int)
+    kz, ky, kx = np.meshgrid(k, k, k, indexing="ij")
+    div = kx * Fh[0] + ky * Fh[1] + kz * Fh[2]
+    assert np.abs(div).max() <= 1e-12 * np.abs(Fh).max()
+    own_axis = {0: 2, 1: 1, 2: 0}  # array axis (of z, y, x) of component i's own coordinate
+    for i in range(3):
+        assert abs(F[i].sum()) <= 1e-15
+        assert np.isclose((F[i] ** 2).mean(), F0 ** 2 / 2, rtol=1e-12)
+        assert np.isclose(np.abs(F[i]).max(), F0, rtol=1e-12)
+        P = np.abs(Fh[i]) ** 2
+        modes = np.argwhere(P > 1e-20 * P.max())
+        assert len(modes) == 2  # +k and -k of one wave vector
+        kvec = [tuple(int(k[j]) for j in m) for m in modes]  # (kz, ky, kx)
+        nonzero_axes = {a for kv in kvec for a in range(3) if kv[a] != 0}
+        assert len(nonzero_axes) == 1
+        (ax,) = nonzero_axes
+        assert {abs(kv[ax]) for kv in kvec} == {1}
+        assert ax != own_axis[i]
