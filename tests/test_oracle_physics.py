@@ -351,3 +351,26 @@ def test_shear_wave_advected_by_a_uniform_flow():
     assert np.isclose(np.log(abs(c1) / abs(c0)), -nu0 * k * k * T, rtol=1e-2)
     dphi = np.angle(c1 / c0) + k * U * T
     assert abs((dphi + np.pi) % (2 * np.pi) - np.pi) <= 1e-3
+
+
+def test_smagorinsky_kolmogorov_flow_closed_form():
+    """Kolmogorov flow with the Smagorinsky closure (C = 0.1): in the steady
+    state the momentum balance of Eqs. (eddy_visc), (les_viscosity) integrates
+    once to (nu0 + C |u'|) u' = (F0 / k) cos(k y), whose root gives the strain
+    |S| = |u'| cell by cell and theta = 3 (nu0 + C |S|).  Forcing chosen so that
+    the eddy viscosity equals nu0 at the peak: the peak strain is half the
+    C = 0 value, so a squared C, a missing eddy viscosity or a wrong |S|
+    convention fails by tens of per cent.  Gates: 2 % (|S|), 1 % (theta)."""
+    ny, nu0, C, smax = 16, 0.001, 0.1, 0.01
+    k = 2 * np.pi / ny
+    F0 = (nu0 + C * smax) * smax * k
+    L = oracle.OracleLBM(1, ny, 1, nu0, C, oracle.FORCE_KOLMOGOROV, F0=F0)
+    L.init_equilibrium(np.zeros((3, 1, ny, 1)))
+    L.step(int(12 / ((nu0 + 0.5 * C * smax) * k * k)))
+    fl = L.fields()
+    c = (F0 / k) * np.cos(k * np.arange(ny))
+    du = np.sign(c) * (np.sqrt(nu0 ** 2 + 4 * C * np.abs(c)) - nu0) / (2 * C)
+    sn, th = fl["snorm"][0, :, 0], fl["theta"][0, :, 0]
+    assert np.abs(sn - np.abs(du)).max() <= 0.02 * smax
+    assert np.abs(th - 3 * (nu0 + C * np.abs(du))).max() <= 0.01 * th.max()
+    assert np.isclose(np.abs(du).max(), 0.5 * F0 / (nu0 * k))
