@@ -421,3 +421,26 @@ def test_grouped_copies_across_uneven_instances(gpu_lib):
             refs[i].init_equilibrium(inits[i])
             refs[i].step(17)
             assert full_f_rel_error(g.populations(inst=i), refs[i].populations()) <= 1e-5, i
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_smagorinsky_kolmogorov_flow_closed_form(gpu_lib, kind):
+    """The CUDA path against physics rather than the oracle: Kolmogorov flow
+    with the Smagorinsky closure (C = 0.1) reaches the steady state of
+    (nu0 + C |u'|) u' = (F0 / k) cos(k y), |S| = |u'| and theta =
+    3 (nu0 + C |S|) cell by cell (the eddy viscosity halves the peak strain
+    here).  Gates: 2 % (|S|), 1 % (theta), as for the oracle."""
+    lbm = gpu_lib
+    ny, nu0, C, smax = 16, 0.001, 0.1, 0.01
+    k = 2 * np.pi / ny
+    F0 = (nu0 + C * smax) * smax * k
+    gpu, _ = make_pair(lbm, (1, ny, 1), nu0=nu0, C=C, force_mode=lbm.LBM_FORCE_KOLMOGOROV, F0=F0, kind=kind)
+    with gpu:
+        gpu.init(lbm.LBM_INIT_REST)
+        gpu.step(int(12 / ((nu0 + 0.5 * C * smax) * k * k)))
+        fl = gpu.fields()
+    c = (F0 / k) * np.cos(k * np.arange(ny))
+    du = np.sign(c) * (np.sqrt(nu0 ** 2 + 4 * C * np.abs(c)) - nu0) / (2 * C)
+    sn, th = fl["snorm"][0, :, 0], fl["theta"][0, :, 0]
+    assert np.abs(sn - np.abs(du)).max() <= 0.02 * smax
+    assert np.abs(th - 3 * (nu0 + C * np.abs(du))).max() <= 0.01 * th.max()
