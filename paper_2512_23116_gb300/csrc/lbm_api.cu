@@ -728,9 +728,9 @@ struct Candidate {
 // (row_stage = 19 x-lines of the widest instance), else the runtime stride.
 Candidate tma_candidate(int64_t row_stage, int R, int stages, int threads, bool slots = true) {
   const int64_t seg = row_stage / 19 * R;  // bytes of R x-lines of one population
-  if (slots && stages == 3 && seg <= kSlot3) return {2, threads, stages, 19 * kSlot3, R, kSlot3};
-  if (slots && stages == 2 && seg <= kSlot2) return {2, threads, stages, 19 * kSlot2, R, kSlot2};
-  return {2, threads, stages, (int)((row_stage * R + 15) / 16 * 16), R, 0};
+  if (slots && stages == 3 && seg <= kSlot3) return {2, threads, stages, 19 * kSlot3, R, kSlot3, 0};
+  if (slots && stages == 2 && seg <= kSlot2) return {2, threads, stages, 19 * kSlot2, R, kSlot2, 0};
+  return {2, threads, stages, (int)((row_stage * R + 15) / 16 * 16), R, 0, 0};
 }
 
 int apply_candidate(lbm_t h, const Candidate& c) {
