@@ -444,3 +444,52 @@ def test_smagorinsky_kolmogorov_flow_closed_form(gpu_lib, kind):
     sn, th = fl["snorm"][0, :, 0], fl["theta"][0, :, 0]
     assert np.abs(sn - np.abs(du)).max() <= 0.02 * smax
     assert np.abs(th - 3 * (nu0 + C * np.abs(du))).max() <= 0.01 * th.max()
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_sound_wave_speed_and_bulk_viscosity(gpu_lib, kind):
+    """The CUDA path against physics: a standing sound wave oscillates at
+    c_s k (c_s^2 = 1/3) and decays at (k^2 / 2)(4 nu / 3 + zeta), zeta =
+    (2/9)(1/s1 - 1/2), s1 = 1.19 (64 x 1 x 1 box, 2000 steps, Prony fit)."""
+    lbm = gpu_lib
+    n, nu0, A = 64, 0.01, 1e-5
+    k = 2 * np.pi / n
+    x = np.arange(n)
+    gpu, ref = make_pair(lbm, (1, 1, n), nu0=nu0, C=0.0, kind=kind)
+    ref.init_equilibrium(np.zeros((3, 1, 1, n)), (A * np.cos(k * x)).reshape(1, 1, n))
+    T = 2000
+    a = np.zeros(T + 1)
+    with gpu:
+        gpu.set_populations(ref.populations())
+        for t in range(T + 1):
+            if t:
+                gpu.step(1)
+            a[t] = 2.0 / n * np.dot(gpu.fields()["drho"].reshape(n), np.cos(k * x))
+    c1, c2 = np.linalg.lstsq(np.stack([a[1:-1], a[:-2]], 1), a[2:], rcond=None)[0]
+    r = np.sqrt(-c2)
+    gamma, omega = -np.log(r), np.arccos(c1 / (2 * r))
+    zeta = 2.0 / 9.0 * (1.0 / 1.19 - 0.5)
+    assert np.isclose(omega, k / np.sqrt(3.0), rtol=5e-3)
+    assert np.isclose(gamma, 0.5 * k * k * (4.0 * nu0 / 3.0 + zeta), rtol=1e-2)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_shear_wave_advected_by_a_uniform_flow(gpu_lib, kind):
+    """The CUDA path against physics: a shear wave carried by a uniform flow
+    U = 0.05 travels at U and decays at nu k^2 (64 x 1 x 1 box, 1000 steps)."""
+    lbm = gpu_lib
+    n, nu0, A, U, T = 64, 0.01, 1e-4, 0.05, 1000
+    k = 2 * np.pi / n
+    x = np.arange(n)
+    u = np.zeros((3, 1, 1, n))
+    u[0] = U
+    u[1, 0, 0, :] = A * np.sin(k * x)
+    gpu, _ = make_pair(lbm, (1, 1, n), nu0=nu0, C=0.0, kind=kind)
+    with gpu:
+        gpu.init(lbm.LBM_INIT_VELOCITY, u=u)
+        c0 = 2.0 / n * np.sum(gpu.fields()["u"][1].reshape(n) * np.exp(-1j * k * x))
+        gpu.step(T)
+        c1 = 2.0 / n * np.sum(gpu.fields()["u"][1].reshape(n) * np.exp(-1j * k * x))
+    assert np.isclose(np.log(abs(c1) / abs(c0)), -nu0 * k * k * T, rtol=1e-2)
+    dphi = np.angle(c1 / c0) + k * U * T
+    assert abs((dphi + np.pi) % (2 * np.pi) - np.pi) <= 1e-3
