@@ -127,7 +127,9 @@ struct HistRun {
 // Reduce the accumulators of the `nthreads` threads that call this (a whole
 // block, or the consumer warps of a specialised block synchronised with named
 // barrier `bar_id`) and write kNP doubles to dst.  Fixed order: lane tree,
-// then warps in index order.
+// then warps in index order.  Inlined into its kernel: an out-of-line call
+// takes the accumulator's address, which keeps its sums in local memory for
+// the whole cell loop.
 __device__ __forceinline__ void named_sync(int bar_id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(nthreads) : "memory");
 }
