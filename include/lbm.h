@@ -182,6 +182,17 @@ int lbm_create(const lbm_params* params, lbm_t* out);
  * Errors as lbm_create; UNSUPPORTED if precisions or devices differ. */
 int lbm_create_batch(const lbm_params* params, int32_t count, lbm_t* out);
 
+/* The batch entry points under their ensemble names (Sec. 3: statistics of
+ * independent forced-HIT runs; no counterpart in the paper's solver, which runs
+ * one box): lbm_batch_create is lbm_create_batch; lbm_batch_step(h, n)
+ * advances every instance by n steps in the same launches as lbm_step;
+ * lbm_batch_stats(h, what, out) fills out[i] (caller-owned, lbm_count(h)
+ * entries) with lbm_stats of instance i, stopping at the first error.
+ * Errors as the functions they stand for. */
+int lbm_batch_create(const lbm_params* params, int32_t count, lbm_t* out);
+int lbm_batch_step(lbm_t h, int64_t n);
+int lbm_batch_stats(lbm_t h, int32_t what, lbm_stats_t* out);
+
 /* Release every device resource of the handle.  Accepts NULL. */
 int lbm_destroy(lbm_t h);
 
@@ -281,6 +292,12 @@ int lbm_set_time(lbm_t h, int64_t t);
  * tau_e - 1/2 [nz][ny][nx].  Computed in FP32 by the read-only step pass. */
 int lbm_get_fields(lbm_t h, int32_t inst, double* drho, double* u, double* snorm,
                    double* theta);
+
+/* The Guo-corrected velocity u = (sum_a f_a c_a + F/2) / rho (Eq. guo_velocity)
+ * of `inst` at the current time into the caller-owned FP64 host array
+ * u[3][nz][ny][nx]: lbm_get_fields with only u requested.  Synchronous.
+ * Errors: INVALID_ARG (null handle or output, instance out of range), CUDA. */
+int lbm_get_velocity(lbm_t h, int32_t inst, double* u);
 
 /* One plane of theta = tau_e - 1/2 (the K_t map of Sec. 4.1): axis 0, 1, 2 =
  * the plane x = index, y = index or z = index; host array of the plane's two

@@ -40,7 +40,7 @@ EXPORTED = [
     "lbm_get_populations", "lbm_set_populations", "lbm_set_time", "lbm_get_fields",
     "lbm_get_theta_slice", "lbm_device_ptr", "lbm_get_params", "lbm_kernel_config",
     "lbm_last_error", "lbm_version", "lbm_structure_functions_noalloc", "lbm_debug_withhold_load",
-    "lbm_energy_balance",
+    "lbm_energy_balance", "lbm_batch_create", "lbm_batch_step", "lbm_batch_stats", "lbm_get_velocity",
 ]
 
 
@@ -161,6 +161,10 @@ def load():
                                              ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
         "lbm_debug_withhold_load": ([H, ctypes.c_double], ctypes.c_int),
         "lbm_energy_balance": ([ctypes.POINTER(LbmRecord), i32, _D, ctypes.POINTER(i64)], ctypes.c_int),
+        "lbm_batch_create": ([ctypes.POINTER(LbmParams), i32, ctypes.POINTER(H)], ctypes.c_int),
+        "lbm_batch_step": ([H, i64], ctypes.c_int),
+        "lbm_batch_stats": ([H, i32, ctypes.POINTER(LbmStats)], ctypes.c_int),
+        "lbm_get_velocity": ([H, i32, _D], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -334,6 +338,30 @@ def lbm_get_fields(h, inst: int, shape) -> dict:
     th = np.zeros((nz, ny, nx))
     _check(h, load().lbm_get_fields(h, inst, _ptr(drho), _ptr(u), _ptr(sn), _ptr(th)))
     return {"drho": drho, "u": u, "snorm": sn, "theta": th}
+
+
+def lbm_get_velocity(h, inst: int, shape) -> np.ndarray:
+    nz, ny, nx = shape
+    u = np.zeros((3, nz, ny, nx))
+    _check(h, load().lbm_get_velocity(h, inst, _ptr(u)))
+    return u
+
+
+def lbm_batch_create(params: list) -> ctypes.c_void_p:
+    arr = (LbmParams * len(params))(*params)
+    h = ctypes.c_void_p()
+    _check(None, load().lbm_batch_create(arr, len(params), ctypes.byref(h)))
+    return h
+
+
+def lbm_batch_step(h, n: int) -> None:
+    _check(h, load().lbm_batch_step(h, n))
+
+
+def lbm_batch_stats(h, count: int, what: int = 0) -> list:
+    out = (LbmStats * max(count, 1))()
+    _check(h, load().lbm_batch_stats(h, what, out))
+    return [out[i].as_dict() for i in range(count)]
 
 
 def lbm_get_theta_slice(h, inst: int, axis: int, index: int, shape) -> np.ndarray:

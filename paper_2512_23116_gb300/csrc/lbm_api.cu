@@ -898,6 +898,10 @@ LBM_API int lbm_create_batch(const lbm_params* params, int32_t count, lbm_t* out
   return create_impl(params, count, out);
 }
 
+LBM_API int lbm_batch_create(const lbm_params* params, int32_t count, lbm_t* out) {
+  return create_impl(params, count, out);
+}
+
 LBM_API int lbm_destroy(lbm_t h) {
   if (!h) return LBM_OK;
   DevGuard g(h->device);
@@ -1018,6 +1022,8 @@ LBM_API int lbm_step(lbm_t h, int64_t n) {
   return run_steps(h, n);
 }
 
+LBM_API int lbm_batch_step(lbm_t h, int64_t n) { return lbm_step(h, n); }
+
 LBM_API int lbm_sync(lbm_t h) {
   if (!h) return fail(nullptr, LBM_ERR_INVALID_ARG, "null handle");
   DevGuard g(h->device);
@@ -1103,6 +1109,16 @@ LBM_API int lbm_stats(lbm_t h, int32_t inst, int32_t what, lbm_stats_t* out) {
       for (int q = 0; q < 6; ++q) out->Sp[k][q] = sp[q] / (3.0 * (double)I.ncell);
       out->F4[k] = out->Sp[k][3] / (out->Sp[k][1] * out->Sp[k][1]);  // Eq. (flatness)
     }
+  }
+  return LBM_OK;
+}
+
+LBM_API int lbm_batch_stats(lbm_t h, int32_t what, lbm_stats_t* out) {
+  if (!h) return fail(nullptr, LBM_ERR_INVALID_ARG, "null handle");
+  if (!out) return fail(h, LBM_ERR_INVALID_ARG, "null output");
+  for (int i = 0; i < (int)h->inst.size(); ++i) {
+    const int rc = lbm_stats(h, i, what, out + i);
+    if (rc != LBM_OK) return rc;
   }
   return LBM_OK;
 }
@@ -1266,6 +1282,12 @@ LBM_API int lbm_get_fields(lbm_t h, int32_t inst, double* drho, double* u, doubl
   if (snorm && (rc = fetch(I.aux + I.ncell, snorm, I.ncell)) != LBM_OK) return rc;
   if (theta && (rc = fetch(I.aux + 2 * I.ncell, theta, I.ncell)) != LBM_OK) return rc;
   return check_err(h);
+}
+
+LBM_API int lbm_get_velocity(lbm_t h, int32_t inst, double* u) {
+  CHECK_INST(h, inst);
+  if (!u) return fail(h, LBM_ERR_INVALID_ARG, "null output");
+  return lbm_get_fields(h, inst, nullptr, u, nullptr, nullptr);
 }
 
 LBM_API int lbm_get_theta_slice(lbm_t h, int32_t inst, int32_t axis, int32_t index, double* host) {

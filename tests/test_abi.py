@@ -128,3 +128,20 @@ def test_energy_balance_host_function(lib):
         lib.lbm_energy_balance(recs[:2])
     with pytest.raises(lib.LbmError):
         lib.lbm_energy_balance([recs[1], recs[0], recs[2]])
+
+
+def test_batch_and_velocity_entry_points_validate_arguments(lib):
+    """lbm_batch_create / lbm_batch_step / lbm_batch_stats / lbm_get_velocity
+    reject bad arguments before any device call, like the functions they
+    stand for."""
+    calls = (lambda: lib.lbm_batch_step(None, 1), lambda: lib.lbm_batch_stats(None, 1),
+             lambda: lib.lbm_get_velocity(None, 0, (2, 2, 2)), lambda: lib.lbm_batch_create([]))
+    for call in calls:
+        with pytest.raises(lib.LbmError) as ei:
+            call()
+        assert ei.value.code == lib.LBM_ERR_INVALID_ARG
+    a = lib.make_params(8, nu0=0.01)
+    b = lib.make_params(8, nu0=0.01, precision=lib.LBM_FP16_SHIFTED)
+    with pytest.raises(lib.LbmError) as ei:
+        lib.lbm_batch_create([a, b])
+    assert ei.value.code == lib.LBM_ERR_UNSUPPORTED

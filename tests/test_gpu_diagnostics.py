@@ -271,3 +271,27 @@ def test_energy_balance_series_matches_oracle(gpu_lib):
     t_ref, r_ref = dg.energy_balance(times, E, inj, eps)
     assert list(at) == list(t_ref)
     assert np.allclose(res, r_ref, atol=1e-4), (res, r_ref)
+
+
+def test_batch_entry_points_and_velocity(gpu_lib):
+    """The ensemble entry points equal the functions they stand for:
+    lbm_batch_stats gives each instance's lbm_stats, lbm_get_velocity the u of
+    lbm_get_fields (same read-only pass, bit for bit)."""
+    lbm = gpu_lib
+    shapes = [(8, 8, 8), (6, 10, 12)]
+    h = lbm.lbm_batch_create([lbm.make_params(nx, ny, nz, nu0=0.01, cs=0.1) for (nz, ny, nx) in shapes])
+    try:
+        for i in range(len(shapes)):
+            lbm.lbm_init_field(h, i, lbm.LBM_INIT_TGV3D, 0.05)
+        lbm.lbm_batch_step(h, 5)
+        st = lbm.lbm_batch_stats(h, len(shapes))
+        for i, shape in enumerate(shapes):
+            one = lbm.lbm_stats(h, i)
+            assert st[i]["step"] == 5 and st[i]["cells"] == int(np.prod(shape))
+            for k in ("E_k", "eps0", "eps_sgs", "theta_mean", "mass"):
+                assert st[i][k] == one[k], k
+            u = lbm.lbm_get_velocity(h, i, shape)
+            assert np.array_equal(u, lbm.lbm_get_fields(h, i, shape)["u"])
+            assert np.abs(u).max() > 0.01
+    finally:
+        lbm.lbm_destroy(h)
