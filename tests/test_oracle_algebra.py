@@ -237,3 +237,62 @@ def test_selfconsistent_strain_is_a_fixed_point():
         s = oracle.strain_norm_selfconsistent(m, 1.19, nu0, C)
         again = oracle.strain_norm(oracle.strain(m, 1.19, 1.0 / (0.5 + 3 * (nu0 + C * s))))
         assert math.isclose(again, s, rel_tol=1e-13)
+
+
+# The relaxation rates printed in Eq. (relaxation-matrix), by moment row: the
+# conserved rows 0, 3, 5, 7 (any rate: m = m^eq there), the energy mode 1, the
+# energy square 2, the heat fluxes 4, 6, 8, the stress rows 9, 11, 13, 14, 15
+# (the shear rate s_nu), their fourth-order partners 10, 12 and the
+# third-order rows 16-18.
+PRINTED_RATES = {1: 1.19, 2: 1.4, 4: 1.2, 6: 1.2, 8: 1.2, 10: 1.4, 12: 1.4, 16: 1.98, 17: 1.98, 18: 1.98}
+SHEAR_ROWS = (9, 11, 13, 14, 15)
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 6, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18])
+@pytest.mark.parametrize("flow", [False, True])
+def test_one_collision_relaxes_each_moment_at_its_rate(k, flow):
+    """Observed, not read from the oracle's rate table: a uniform cell at its
+    equilibrium (at rest, or in a uniform flow) with one moment k moved off
+    equilibrium by delta, no force, C = 0; after one collision of Eq.
+    (mrt_les_guo) the moment's departure is (1 - s_k) delta and every other
+    moment is still at equilibrium.  This observes every rate of Eq.
+    (relaxation-matrix), including the ones without a hydrodynamic effect (s2,
+    s4, s10 = s12, s16-18), and, in a flow, the equilibrium each row relaxes to
+    (e.g. m2 -> -475/63 rho u^2 of Eq. meq_fm)."""
+    nu0 = 0.01
+    s_nu = 1.0 / (0.5 + 3.0 * nu0)  # Eq. (bare_viscosity)
+    s_k = s_nu if k in SHEAR_ROWS else PRINTED_RATES[k]
+    u = np.array([0.03, -0.02, 0.01]) if flow else np.zeros(3)
+    drho = 0.004 if flow else 0.0
+    M = oracle.moment_matrix()
+    m_eq = oracle.meq(drho, u)
+    delta = 1e-3
+    m = m_eq.copy()
+    m[k] += delta
+    fp = np.linalg.solve(M, m)  # library solve: the oracle's own inverse is not used here
+    fstar, _ = oracle.collide_one(fp, np.zeros(3), nu0, 0.0)
+    mstar = M @ fstar
+    want = m_eq.copy()
+    want[k] += (1.0 - s_k) * delta
+    assert np.allclose(mstar, want, rtol=0.0, atol=1e-13), (k, mstar - want)
+
+
+def test_energy_square_relaxes_to_the_printed_equilibrium():
+    """Row 2 in a uniform flow, started at m2 = 0: one collision moves it to
+    s2 m2^eq with m2^eq = -475/63 rho |u|^2 (Eq. meq_fm) and s2 = 1.4 (Eq.
+    relaxation-matrix), values typed from the paper; repeated collisions
+    converge to m2^eq."""
+    u = np.array([0.04, 0.01, -0.03])
+    drho = 0.002
+    rho = 1.0 + drho
+    M = oracle.moment_matrix()
+    m = oracle.meq(drho, u)
+    m[2] = 0.0
+    fp = np.linalg.solve(M, m)
+    f1, _ = oracle.collide_one(fp, np.zeros(3), 0.01, 0.0)
+    eq2 = -475.0 / 63.0 * rho * float(u @ u)
+    assert math.isclose((M @ f1)[2], 1.4 * eq2, rel_tol=1e-12)
+    f = fp
+    for _ in range(40):
+        f, _ = oracle.collide_one(f, np.zeros(3), 0.01, 0.0)
+    assert math.isclose((M @ f)[2], eq2, rel_tol=1e-12)
