@@ -261,9 +261,7 @@ int grid_for(int64_t n) {
 template <typename T, typename U>
 cudaError_t init_t(const InstDesc& d, bool odd, int mode, double amp, const U* u,
                    int64_t ustride, int64_t c0, int64_t n, cudaStream_t st) {
-  (void)cudaGetLastError();
-  k_init<T, U><<<grid_for(n), kAuxThreads, 0, st>>>(d, odd, mode, amp, u, ustride, c0, n);
-  return cudaGetLastError();
+  return launch_kernel(k_init<T, U>, grid_for(n), kAuxThreads, 0, st, d, odd, mode, amp, u, ustride, c0, n);
 }
 
 template <typename U>
@@ -294,28 +292,24 @@ cudaError_t launch_get_pop(const InstDesc& d, int precision, bool odd, int a, do
                            int shifted, int64_t c0, int64_t n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int g = grid_for(n);
-  (void)cudaGetLastError();
   switch (precision) {
-    case 0: k_get_pop<float><<<g, kAuxThreads, 0, st>>>(d, odd, a, out, shifted, c0, n); break;
-    case 1: k_get_pop<__half><<<g, kAuxThreads, 0, st>>>(d, odd, a, out, shifted, c0, n); break;
-    case 2: k_get_pop<__nv_bfloat16><<<g, kAuxThreads, 0, st>>>(d, odd, a, out, shifted, c0, n); break;
-    default: return cudaErrorInvalidValue;
+    case 0: return launch_kernel(k_get_pop<float>, g, kAuxThreads, 0, st, d, odd, a, out, shifted, c0, n);
+    case 1: return launch_kernel(k_get_pop<__half>, g, kAuxThreads, 0, st, d, odd, a, out, shifted, c0, n);
+    case 2: return launch_kernel(k_get_pop<__nv_bfloat16>, g, kAuxThreads, 0, st, d, odd, a, out, shifted, c0, n);
   }
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_set_pop(const InstDesc& d, int precision, bool odd, int a, const double* in,
                            int shifted, int64_t c0, int64_t n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int g = grid_for(n);
-  (void)cudaGetLastError();
   switch (precision) {
-    case 0: k_set_pop<float><<<g, kAuxThreads, 0, st>>>(d, odd, a, in, shifted, c0, n); break;
-    case 1: k_set_pop<__half><<<g, kAuxThreads, 0, st>>>(d, odd, a, in, shifted, c0, n); break;
-    case 2: k_set_pop<__nv_bfloat16><<<g, kAuxThreads, 0, st>>>(d, odd, a, in, shifted, c0, n); break;
-    default: return cudaErrorInvalidValue;
+    case 0: return launch_kernel(k_set_pop<float>, g, kAuxThreads, 0, st, d, odd, a, in, shifted, c0, n);
+    case 1: return launch_kernel(k_set_pop<__half>, g, kAuxThreads, 0, st, d, odd, a, in, shifted, c0, n);
+    case 2: return launch_kernel(k_set_pop<__nv_bfloat16>, g, kAuxThreads, 0, st, d, odd, a, in, shifted, c0, n);
   }
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_relayout_pair(const InstDesc& d, int precision, bool from_odd, int a,
@@ -335,30 +329,30 @@ cudaError_t launch_relayout_pair(const InstDesc& d, int precision, bool from_odd
                         row, rows, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
   const int g = grid_for((int64_t)d.nx * d.ny * d.nz);
-  (void)cudaGetLastError();
   switch (precision) {
-    case 0: k_relayout<float><<<g, kAuxThreads, 0, st>>>(d, from_odd, a, (const float*)s, (const float*)(s + plane)); break;
-    case 1: k_relayout<__half><<<g, kAuxThreads, 0, st>>>(d, from_odd, a, (const __half*)s, (const __half*)(s + plane)); break;
-    case 2: k_relayout<__nv_bfloat16><<<g, kAuxThreads, 0, st>>>(d, from_odd, a, (const __nv_bfloat16*)s, (const __nv_bfloat16*)(s + plane)); break;
-    default: return cudaErrorInvalidValue;
+    case 0:
+      return launch_kernel(k_relayout<float>, g, kAuxThreads, 0, st, d, from_odd, a, (const float*)s,
+                           (const float*)(s + plane));
+    case 1:
+      return launch_kernel(k_relayout<__half>, g, kAuxThreads, 0, st, d, from_odd, a, (const __half*)s,
+                           (const __half*)(s + plane));
+    case 2:
+      return launch_kernel(k_relayout<__nv_bfloat16>, g, kAuxThreads, 0, st, d, from_odd, a,
+                           (const __nv_bfloat16*)s, (const __nv_bfloat16*)(s + plane));
   }
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_finish(const double* partials, int ninst, int grid, double* results,
                           double* ring, unsigned long long* seq, int cap, uint32_t* err,
                           cudaStream_t st) {
-  (void)cudaGetLastError();
-  k_finish<<<1, 256, 0, st>>>(partials, ninst, grid, results, ring, seq, cap, err);
-  return cudaGetLastError();
+  return launch_kernel(k_finish, 1, 256, 0, st, partials, ninst, grid, results, ring, seq, cap, err);
 }
 
 cudaError_t launch_spec_bin(const void* coeffs, int nx, int ny, int nz, int kmax,
                             double* partials, int blocks, cudaStream_t st) {
-  (void)cudaGetLastError();
-  k_spec_bin<<<blocks, kAuxThreads, (size_t)(kmax + 1) * sizeof(double), st>>>(
-      static_cast<const float2*>(coeffs), nx, ny, nz, kmax, partials);
-  return cudaGetLastError();
+  return launch_kernel(k_spec_bin, blocks, kAuxThreads, (size_t)(kmax + 1) * sizeof(double), st,
+                       static_cast<const float2*>(coeffs), nx, ny, nz, kmax, partials);
 }
 
 cudaError_t launch_spec_finish(const double* partials, int blocks, int kmax, double* E,
@@ -368,16 +362,12 @@ cudaError_t launch_spec_finish(const double* partials, int blocks, int kmax, dou
 
 cudaError_t launch_sum_cols(const double* partials, int rows, int cols, double* out,
                             cudaStream_t st) {
-  (void)cudaGetLastError();
-  k_sum_cols<<<(cols + 255) / 256, 256, 0, st>>>(partials, rows, cols, out);
-  return cudaGetLastError();
+  return launch_kernel(k_sum_cols, (cols + 255) / 256, 256, 0, st, partials, rows, cols, out);
 }
 
 cudaError_t launch_struct(const float* u, int nx, int ny, int nz, int r, double* partials,
                           int blocks, cudaStream_t st) {
-  (void)cudaGetLastError();
-  k_struct<<<blocks, kAuxThreads, 0, st>>>(u, nx, ny, nz, r, partials);
-  return cudaGetLastError();
+  return launch_kernel(k_struct, blocks, kAuxThreads, 0, st, u, nx, ny, nz, r, partials);
 }
 
 }  // namespace lbm

@@ -63,6 +63,9 @@ struct StatsArgs {
 // Error bits of the device error word.
 constexpr uint32_t ERR_NONFINITE = 1u;
 constexpr uint32_t ERR_TIMEOUT = 2u;
+// After a timeout, loads already issued had not landed within the drain bound
+// (kDrainRounds x wait_ns) when the block left.
+constexpr uint32_t ERR_DRAIN = 4u;
 
 // Step kernel modes.
 enum { MODE_STEP = 0, MODE_STEP_STATS = 1, MODE_DIAG = 2 };

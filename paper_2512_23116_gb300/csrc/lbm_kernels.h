@@ -4,10 +4,28 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <utility>
 
 #include "lbm_internal.h"
 
 namespace lbm {
+
+// Launch `kernel` and return the status of this launch alone.  A <<<...>>>
+// launch reports only through cudaGetLastError(), which also returns (and
+// clears) any error the caller's own earlier work left pending on the thread;
+// cudaLaunchKernelEx returns the launch's status and leaves that state alone.
+template <typename... P, typename... A>
+inline cudaError_t launch_kernel(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                 A&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = nullptr;
+  cfg.numAttrs = 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
 
 struct LaunchArgs {
   const InstDesc* insts;   // device table
@@ -94,5 +112,15 @@ cudaError_t launch_struct(const float* u, int nx, int ny, int nz, int r, double*
                           int blocks, cudaStream_t st);
 cudaError_t launch_sum_cols(const double* partials, int rows, int cols, double* out,
                             cudaStream_t st);
+
+// Seeded random solenoidal velocity (lbm_random_field.cu): the FP32 field
+// u[3][nz][ny][nx] (device memory, 3 nx ny nz floats) of the recipe described
+// there.  Allocates and frees its own FP64 / complex work buffers and a cuFFT
+// plan; synchronises the stream.  Returns null on success, else the failed
+// step (*cuda_err: the CUDA error, cudaErrorUnknown for a cuFFT failure).
+const char* random_velocity_f32(int nx, int ny, int nz, uint64_t seed, double urms, double k0, float* u,
+                                cudaStream_t st, cudaError_t* cuda_err);
+// Largest |k| of the random field's modes: max(1, min(n_min / 2 - 1, floor(6 k0))).
+int random_field_cutoff(int nx, int ny, int nz, double k0);
 
 }  // namespace lbm

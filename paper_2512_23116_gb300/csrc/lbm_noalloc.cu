@@ -70,6 +70,28 @@ int reject(int code, const char* msg) {
   return code;
 }
 
+// True when [p, p + bytes) starts and ends in device (or managed) memory of
+// device `dev`: both ends are looked up with cudaPointerGetAttributes, which
+// allocates nothing.  A host pointer, a pointer of another device or an
+// unknown address is rejected before any launch (a kernel given one would
+// fault).  A lookup failure this call caused is not left pending on the
+// thread; an error the caller left pending is not touched.
+bool device_range(const void* p, size_t bytes, int dev) {
+  const bool pending = cudaPeekAtLastError() != cudaSuccess;
+  const char* ends[2] = {static_cast<const char*>(p), static_cast<const char*>(p) + bytes - 1};
+  for (const char* q : ends) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, q) != cudaSuccess) {
+      if (!pending) (void)cudaGetLastError();
+      return false;
+    }
+    if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != dev ||
+        !at.devicePointer)
+      return false;
+  }
+  return true;
+}
+
 }  // namespace
 
 LBM_API int lbm_structure_functions_noalloc(const float* u, int32_t nx, int32_t ny, int32_t nz,
@@ -82,18 +104,24 @@ LBM_API int lbm_structure_functions_noalloc(const float* u, int32_t nx, int32_t 
                   "nr must be between 1 and 24: the fixed scratch holds 24 separations");
   for (int k = 0; k < nr; ++k)
     if (r[k] < 1) return reject(LBM_ERR_INVALID_ARG, "separations must be >= 1");
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return reject(LBM_ERR_CUDA, cudaGetErrorString(e));
+  const size_t ncell = (size_t)nx * (size_t)ny * (size_t)nz;
+  if (!device_range(u, 3 * ncell * sizeof(float), dev))
+    return reject(LBM_ERR_INVALID_ARG, "u must be device memory of the current device (3 nx ny nz floats)");
+  if (!device_range(sp, (size_t)nr * 6 * sizeof(double), dev))
+    return reject(LBM_ERR_INVALID_ARG, "sp must be device memory of the current device (nr x 6 doubles)");
   double* scratch = nullptr;
-  cudaError_t e = scratch_address(&scratch);
+  e = scratch_address(&scratch);
   if (e != cudaSuccess) return reject(LBM_ERR_CUDA, cudaGetErrorString(e));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   for (int k = 0; k < nr; ++k) {
     e = lbm::launch_struct(u, nx, ny, nz, r[k], scratch + (size_t)k * kBlocks * 6, kBlocks, st);
     if (e != cudaSuccess) return reject(LBM_ERR_CUDA, cudaGetErrorString(e));
   }
-  const double inv_count = 1.0 / (3.0 * (double)nx * (double)ny * (double)nz);
-  (void)cudaGetLastError();
-  k_sf_finish<<<1, 160, 0, st>>>(scratch, nr, kBlocks, inv_count, sp);
-  e = cudaGetLastError();
+  const double inv_count = 1.0 / (3.0 * (double)ncell);
+  e = lbm::launch_kernel(k_sf_finish, 1, 160, 0, st, (const double*)scratch, nr, kBlocks, inv_count, sp);
   if (e != cudaSuccess) return reject(LBM_ERR_CUDA, cudaGetErrorString(e));
   return LBM_OK;
 }

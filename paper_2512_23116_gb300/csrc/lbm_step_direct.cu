@@ -126,10 +126,8 @@ static cudaError_t launch_direct_t(const LaunchArgs& la, cudaStream_t st) {
   const size_t smem = (MODE == MODE_DIAG && la.dout.hist && la.dout.hist_bins < kSmemHistBins)
                           ? (size_t)(la.dout.hist_bins + 1) * 4
                           : 0;
-  (void)cudaGetLastError();  // errors of earlier calls were reported by their return codes
-  k_step_direct<T, ODD, MODE><<<la.grid, la.threads, smem, st>>>(la.insts, la.ninst, la.tile_lo,
-                                                                   la.tile_hi, la.sa, la.dout);
-  return cudaGetLastError();
+  return launch_kernel(k_step_direct<T, ODD, MODE>, la.grid, la.threads, smem, st, la.insts, la.ninst,
+                       la.tile_lo, la.tile_hi, la.sa, la.dout);
 }
 
 template <typename T>

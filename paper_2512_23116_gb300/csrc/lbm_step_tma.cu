@@ -53,6 +53,8 @@ namespace lbm {
 namespace {
 
 constexpr int kBarBytes = 128;  // mbarriers + abort flag
+// Bound of the drain after an abort, in units of the launch's wait_ns.
+constexpr int kDrainRounds = 4;
 
 // Per population j: the slot read by the odd step (opp j) and the row shift
 // (cy_j, cz_j), for the producer lanes (one lane per segment).
@@ -563,10 +565,15 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
       }
     }
     if (aborted && lane == 0) {
-      // loads issued but never consumed: wait (bounded) for them to land
+      // loads issued but never consumed target this block's shared memory and
+      // must land before it leaves: wait for each in rounds of wait_ns, at most
+      // kDrainRounds of them; one still missing after that sets ERR_DRAIN
       for (int k = stored; k < loaded; ++k) {
         if (withheld && k == 0) continue;
-        (void)mbar_wait(bar_full + 8u * (k % stages), (uint32_t)((k / stages) & 1), wait_ns);
+        bool landed = false;
+        for (int round = 0; round < kDrainRounds && !landed; ++round)
+          landed = mbar_wait(bar_full + 8u * (k % stages), (uint32_t)((k / stages) & 1), wait_ns);
+        if (!landed) atomicOr(err, ERR_DRAIN);
       }
     }
     bulk_wait_all();
@@ -670,11 +677,9 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
 
 template <typename T, bool ODD, int MODE, int SLOT>
 cudaError_t launch_tma_t(const LaunchArgs& la, cudaStream_t st) {
-  (void)cudaGetLastError();  // errors of earlier calls were reported by their return codes
-  k_step_tma<T, ODD, MODE, SLOT><<<la.grid, la.threads, la.smem_bytes, st>>>(
-      la.insts, la.ninst, la.tile_lo, la.tile_hi, la.sa, la.stages, la.tile_bytes_max, la.err,
-      la.wait_ns, la.withhold_first_load, la.dout, la.hist_smem);
-  return cudaGetLastError();
+  return launch_kernel(k_step_tma<T, ODD, MODE, SLOT>, la.grid, la.threads, la.smem_bytes, st, la.insts,
+                       la.ninst, la.tile_lo, la.tile_hi, la.sa, la.stages, la.tile_bytes_max, la.err,
+                       la.wait_ns, la.withhold_first_load, la.dout, la.hist_smem);
 }
 
 template <typename T, int SLOT>
