@@ -225,6 +225,29 @@ int lbm_init_field(lbm_t h, int32_t inst, int32_t mode, double amplitude,
  * the paper (an input format).  Errors: INVALID_ARG, CUDA. */
 int lbm_init_velocity_f32(lbm_t h, int32_t inst, const float* u, int32_t u_on_device);
 
+/* Set instance `inst` to the local equilibrium of a seeded random solenoidal
+ * velocity field generated on the device.  The paper's runs start from a
+ * Taylor-Green field (Sec. 3.1) and are analysed in a statistically stationary
+ * forced state; this field stands in for such states as a synthetic input:
+ *   modes 0 < |k| <= kc, kc = max(1, min(n_min/2 - 1, floor(6 k0))), half space
+ *   kz > 0 | (kz = 0, ky > 0) | (kz = ky = 0, kx > 0) with conjugate partners;
+ *   per mode and component a complex standard normal (Box-Muller of uniforms
+ *   from SplitMix64 applied twice to a counter of (seed mod 2^32, k, component,
+ *   draw)); projected normal to k (divergence-free); integer shell
+ *   s = round(|k|) scaled to the energy s^4 exp(-2 (s/k0)^2); a global factor
+ *   so that u_rms = sqrt(<u.u>/3) = urms; u(x) = sum_k u_hat(k) e^{2 pi i k.x/n}
+ *   by a cuFFT complex-to-real transform in FP64, rounded to FP32.
+ * Deterministic: the same seed gives the same field on every run.  u_out (may
+ * be NULL) receives that FP32 velocity [3][nz][ny][nx]: host memory
+ * (u_out_on_device = 0) or device memory of the handle's device (1).
+ * Allocates its work buffers (about 28 bytes per cell) for the duration of
+ * the call and synchronises the handle's stream.  Resets the step counter
+ * when count == 1.  Errors: INVALID_ARG (urms or k0 not finite and > 0, an
+ * extent < 4, u_out_on_device not 0 or 1), OOM, CUDA (cuFFT failures
+ * included). */
+int lbm_init_random_spectrum(lbm_t h, int32_t inst, uint64_t seed, double urms, double k0,
+                             float* u_out, int32_t u_out_on_device);
+
 /* Advance every instance by n >= 0 time steps of Eq. (mrt_les_guo): collide in
  * moment space, stream with periodic wrap (AA pattern: one population array,
  * even steps write in place, odd steps to the neighbours).  Asynchronous on the
@@ -327,8 +350,9 @@ int lbm_kernel_config(lbm_t h, int32_t* kind, int32_t* tile_rows, int32_t* stage
 /* Test hook for the failure path (no counterpart in the paper): the next
  * TMA-kernel step launch of `h` runs with every device-side wait bounded by
  * wait_seconds, and block 0 never loads its first tile, so that its consumers'
- * wait runs out.  The kernel then records LBM_ERR_TIMEOUT, waits (bounded) for
- * its copies in flight and returns; the next synchronising call reports
+ * wait runs out.  The kernel then records LBM_ERR_TIMEOUT, waits for its copies
+ * in flight (at most 4 x wait_seconds; copies still missing then are reported
+ * in the error text) and returns; the next synchronising call reports
  * LBM_ERR_TIMEOUT and the handle stays usable (re-initialise the state: the
  * withheld tile was not updated).  Nothing faults or hangs.
  * Errors: INVALID_ARG (wait_seconds outside (0, 10]), UNSUPPORTED (the handle
@@ -352,8 +376,12 @@ int lbm_debug_withhold_load(lbm_t h, double wait_seconds);
  * (other streams, other threads) race and must be serialised by the caller.
  * The first call on a device looks up that array's address with the device
  * current; make that first call before any stream capture begins.
- * Errors: INVALID_ARG (null pointer, extents < 1, nr outside [1, 24], r < 1),
- * CUDA; lbm_last_error(NULL) gives the text. */
+ * Before any launch, both ends of u (3 nx ny nz floats) and of sp (nr x 6
+ * doubles) are checked to be device or managed memory of the current device
+ * (cudaPointerGetAttributes, which allocates nothing).
+ * Errors: INVALID_ARG (null pointer, extents < 1, nr outside [1, 24], r < 1,
+ * u or sp not device memory of the current device), CUDA; lbm_last_error(NULL)
+ * gives the text. */
 int lbm_structure_functions_noalloc(const float* u, int32_t nx, int32_t ny, int32_t nz,
                                     const int32_t* r, int32_t nr, double* sp, void* stream);
 

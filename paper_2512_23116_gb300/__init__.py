@@ -41,6 +41,7 @@ EXPORTED = [
     "lbm_get_theta_slice", "lbm_device_ptr", "lbm_get_params", "lbm_kernel_config",
     "lbm_last_error", "lbm_version", "lbm_structure_functions_noalloc", "lbm_debug_withhold_load",
     "lbm_energy_balance", "lbm_batch_create", "lbm_batch_step", "lbm_batch_stats", "lbm_get_velocity",
+    "lbm_init_random_spectrum",
 ]
 
 
@@ -165,6 +166,8 @@ def load():
         "lbm_batch_step": ([H, i64], ctypes.c_int),
         "lbm_batch_stats": ([H, i32, ctypes.POINTER(LbmStats)], ctypes.c_int),
         "lbm_get_velocity": ([H, i32, _D], ctypes.c_int),
+        "lbm_init_random_spectrum": ([H, i32, ctypes.c_uint64, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_void_p, i32], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -268,6 +271,25 @@ def lbm_init_field(h, inst: int, mode: int, amplitude: float = 0.0, u=None) -> N
     f32 = getattr(u, "dtype", None) == np.float32
     ua = np.ascontiguousarray(u, dtype=np.float32 if f32 else np.float64)
     call(ua.ctypes.data_as(ctypes.c_void_p), 0, f32)
+
+
+def lbm_init_random_spectrum(h, inst: int = 0, seed: int = 1, urms: float = 0.05, k0: float = 4.0,
+                             u_out=None) -> None:
+    """Seeded random solenoidal field generated on the device (include/lbm.h).
+    u_out: None, a float32 numpy array (3, nz, ny, nx), or a contiguous float32
+    torch tensor of that shape (CUDA: device copy; CPU: host copy)."""
+    where, ptr = 0, None
+    if u_out is not None:
+        if hasattr(u_out, "is_cuda"):
+            import torch
+            if u_out.dtype != torch.float32 or not u_out.is_contiguous():
+                raise ValueError("u_out must be a contiguous float32 tensor")
+            where, ptr = (1 if u_out.is_cuda else 0), ctypes.c_void_p(u_out.data_ptr())
+        else:
+            if u_out.dtype != np.float32 or not u_out.flags["C_CONTIGUOUS"]:
+                raise ValueError("u_out must be a C-contiguous float32 array")
+            ptr = u_out.ctypes.data_as(ctypes.c_void_p)
+    _check(h, load().lbm_init_random_spectrum(h, inst, int(seed), float(urms), float(k0), ptr, where))
 
 
 def lbm_step(h, n: int) -> None:
@@ -399,15 +421,19 @@ def lbm_structure_functions_noalloc(u, r, sp, stream=None) -> None:
     u: CUDA float32 tensor (3, nz, ny, nx); r: separations (<= 24 of them);
     sp: CUDA float64 tensor with len(r) * 6 elements, written asynchronously on
     `stream` (a torch stream, or None for the default stream)."""
-    if u.dtype.itemsize != 4 or not u.is_contiguous() or u.dim() != 4 or u.shape[0] != 3:
+    import torch
+    if not (u.is_cuda and sp.is_cuda) or u.device != sp.device:
+        raise ValueError("u and sp must be CUDA tensors on the same device")
+    if u.dtype != torch.float32 or not u.is_contiguous() or u.dim() != 4 or u.shape[0] != 3:
         raise ValueError("u must be a contiguous float32 tensor of shape (3, nz, ny, nx)")
-    if sp.dtype.itemsize != 8 or not sp.is_contiguous():
-        raise ValueError("sp must be a contiguous float64 tensor")
+    if sp.dtype != torch.float64 or not sp.is_contiguous() or sp.numel() < 6 * len(r):
+        raise ValueError("sp must be a contiguous float64 tensor of at least 6 * len(r) elements")
     _, nz, ny, nx = u.shape
     ra = (ctypes.c_int32 * max(1, len(r)))(*r)
     st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
-    _check(None, load().lbm_structure_functions_noalloc(
-        ctypes.c_void_p(u.data_ptr()), nx, ny, nz, ra, len(r), ctypes.c_void_p(sp.data_ptr()), st))
+    with torch.cuda.device(u.device):  # the entry point works on the current device
+        _check(None, load().lbm_structure_functions_noalloc(
+            ctypes.c_void_p(u.data_ptr()), nx, ny, nz, ra, len(r), ctypes.c_void_p(sp.data_ptr()), st))
 
 
 def lbm_energy_balance(records: list):
@@ -471,6 +497,9 @@ class Lattice:
 
     def init(self, mode=LBM_INIT_VELOCITY, amplitude=0.0, u=None, inst=0):
         lbm_init_field(self.h, inst, mode, amplitude, u)
+
+    def init_random(self, seed=1, urms=0.05, k0=4.0, inst=0, u_out=None):
+        lbm_init_random_spectrum(self.h, inst, seed, urms, k0, u_out)
 
     def step(self, n=1):
         lbm_step(self.h, n)

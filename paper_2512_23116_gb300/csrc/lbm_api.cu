@@ -390,12 +390,14 @@ int run_steps(lbm_t h, int64_t n) {
       auto it = h->graphs.find(key);
       if (it == h->graphs.end()) {
         cudaGraph_t g = nullptr;
+        const bool pending = cudaPeekAtLastError() != cudaSuccess;  // the caller's, left alone
         CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         rc = enqueue_steps(h, t0, len);
         cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
         if (rc != LBM_OK) {
           if (g) cudaGraphDestroy(g);
-          (void)cudaGetLastError();  // the invalidated capture; the cause is in h->err
+          // the invalidated capture's own error; the cause is in h->err
+          if (!pending) (void)cudaGetLastError();
           return rc;
         }
         CK(h, ce);
@@ -427,6 +429,10 @@ int check_err(lbm_t h) {
   if (e) {
     CK(h, cudaMemsetAsync(h->d_err, 0, sizeof(uint32_t), h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
+    if (e & ERR_DRAIN)
+      return fail(h, LBM_ERR_TIMEOUT,
+                  "a device-side wait of the step kernel gave up and its copies in flight did not land "
+                  "within the drain bound (error word %u)", e);
     if (e & ERR_TIMEOUT)
       return fail(h, LBM_ERR_TIMEOUT, "a device-side wait of the step kernel gave up (error word %u)", e);
     return fail(h, LBM_ERR_UNSTABLE, "non-finite values in the statistics (error word %u)", e);
@@ -806,6 +812,8 @@ int choose_config(lbm_t h, const lbm_params& p0) {
   }
   // dynamic shared memory left beside the static reduction scratch of the stats variant
   const int64_t smem_cap = 220 * 1024;
+  // shared memory of one SM (228 KB on sm_100 / sm_103; 1 KB of it reserved per block)
+  constexpr int kSmemPerSm = 233472;
   auto fits = [&](int stages, int64_t tb) {
     return (int64_t)tma_smem_bytes(stages, (int)tb, max_nx) <= smem_cap;
   };
@@ -852,6 +860,14 @@ int choose_config(lbm_t h, const lbm_params& p0) {
               Candidate r = tma_candidate(row_stage, R, s, th, false);
               r.layout = 1;
               if (fits(s, r.tile_bytes)) cands.push_back(r);
+            }
+            // two co-resident blocks per SM: stages sized to the tile (runtime
+            // stride) when that leaves room for a second block, so that one
+            // block's pipeline fill and drain overlap the other's steady state
+            if (th == 256 && c.slot_bytes != 0) {
+              Candidate r = tma_candidate(row_stage, R, s, th, false);
+              r.layout = lay;
+              if (2 * (tma_smem_bytes(s, r.tile_bytes, max_nx) + 1024) <= kSmemPerSm) cands.push_back(r);
             }
           }
         }
@@ -956,11 +972,12 @@ int init_velocity(lbm_t h, int32_t inst, const U* u, int32_t where) {
     // both ends of the 3 ncell values must be page-locked memory the device can address
     const U* ends[2] = {u, u + 3 * I.ncell - 1};
     const U* dev_u = nullptr;
+    const bool pending = cudaPeekAtLastError() != cudaSuccess;  // the caller's, left alone
     for (int e = 0; e < 2; ++e) {
       cudaPointerAttributes at{};
-      if (cudaPointerGetAttributes(&at, ends[e]) != cudaSuccess || at.type != cudaMemoryTypeHost ||
-          !at.devicePointer) {
-        (void)cudaGetLastError();
+      const cudaError_t ae = cudaPointerGetAttributes(&at, ends[e]);
+      if (ae != cudaSuccess || at.type != cudaMemoryTypeHost || !at.devicePointer) {
+        if (ae != cudaSuccess && !pending) (void)cudaGetLastError();  // this lookup's own failure
         return fail(h, LBM_ERR_INVALID_ARG, "u_on_device = 2 needs page-locked host memory");
       }
       if (e == 0) dev_u = static_cast<const U*>(at.devicePointer);
@@ -1002,6 +1019,43 @@ LBM_API int lbm_init_field(lbm_t h, int32_t inst, int32_t mode, double amplitude
   const Inst& I = h->inst[inst];
   CK(h, launch_init(h->h_desc[inst], h->precision, (h->t & 1) != 0, mode, amplitude,
                     nullptr, 0, 0, I.ncell, h->stream));
+  return LBM_OK;
+}
+
+LBM_API int lbm_init_random_spectrum(lbm_t h, int32_t inst, uint64_t seed, double urms, double k0,
+                                     float* u_out, int32_t u_out_on_device) {
+  CHECK_INST(h, inst);
+  DevGuard g(h->device);
+  const Inst& I = h->inst[inst];
+  const lbm_params& p = I.p;
+  if (!(urms > 0.0) || !std::isfinite(urms)) return fail(h, LBM_ERR_INVALID_ARG, "urms must be finite and > 0");
+  if (!(k0 > 0.0) || !std::isfinite(k0)) return fail(h, LBM_ERR_INVALID_ARG, "k0 must be finite and > 0");
+  if (p.nx < 4 || p.ny < 4 || p.nz < 4)
+    return fail(h, LBM_ERR_INVALID_ARG, "the random field needs every extent >= 4");
+  if (u_out && (u_out_on_device < 0 || u_out_on_device > 1))
+    return fail(h, LBM_ERR_INVALID_ARG, "u_out_on_device must be 0 or 1");
+  int rc = reset_time(h);
+  if (rc != LBM_OK) return rc;
+  float* u = nullptr;
+  cudaError_t e = cudaMalloc(&u, sizeof(float) * 3 * (size_t)I.ncell);
+  if (e != cudaSuccess)
+    return fail(h, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, "velocity buffer: %s",
+                cudaGetErrorString(e));
+  cudaError_t ce = cudaSuccess;
+  const char* what = random_velocity_f32(p.nx, p.ny, p.nz, seed, urms, k0, u, h->stream, &ce);
+  if (what) {
+    cudaFree(u);
+    return fail(h, ce == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, "random field: %s: %s", what,
+                cudaGetErrorString(ce));
+  }
+  e = init_from(h->h_desc[inst], h->precision, (h->t & 1) != 0, (const float*)u, I.ncell, 0, I.ncell, h->stream);
+  if (e == cudaSuccess && u_out)
+    e = cudaMemcpyAsync(u_out, u, sizeof(float) * 3 * (size_t)I.ncell,
+                        u_out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream);
+  const cudaError_t se = cudaStreamSynchronize(h->stream);
+  cudaFree(u);
+  if (e != cudaSuccess) return fail(h, LBM_ERR_CUDA, "random-field initialisation: %s", cudaGetErrorString(e));
+  if (se != cudaSuccess) return fail(h, LBM_ERR_CUDA, "random-field initialisation: %s", cudaGetErrorString(se));
   return LBM_OK;
 }
 

@@ -1,0 +1,67 @@
+"""Element-wise parity in the launch configurations the benchmark times at the
+paper's own size: the 100^3 LES of Sec. 3.1 / 4.1 (C = 0.13, nu0 = 2.15e-4 from
+Re = 2e4, the paper's forcing of Eqs. forcing_pattern - forcing_amplitude with
+U0 = 0.043, Cf = 0.2), seeded random solenoidal field (k^4 exp(-2 (k/4)^2),
+u_rms = 0.05), 100 steps, FP32 storage, every population of every cell against
+the FP64 oracle: max |f_gpu - f_oracle| / f_oracle <= 1e-5 (full f = f' + w).
+
+The configurations: what the autotuner picks (the bench's 100^3 line runs
+the autotuner), and fixed TMA configurations among its candidates, each
+asserted through lbm_kernel_config: 12 x-lines per tile with two stages of
+5760 B slots and 512 threads (one block per SM), and tiles small enough for
+two co-resident blocks per SM (256 threads)."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+
+from gpu_helpers import full_f_rel_error
+
+pytestmark = pytest.mark.gpu
+
+N, STEPS = 100, 100
+U0, CF, RE, C = 0.043, 0.2, 2.0e4, 0.13
+
+
+@pytest.fixture(scope="module")
+def les_reference():
+    nu0 = U0 * N / RE
+    F0 = oracle.forcing_amplitude(CF, U0, N)
+    u = synthetic.random_solenoidal(N, seed=1, urms=0.05)
+    ref = oracle.OracleLBM(N, N, N, nu0, C, oracle.FORCE_PAPER_SIN, F0=F0)
+    ref.init_equilibrium(u)
+    ref.step(STEPS)
+    return u, nu0, F0, ref.populations()
+
+
+# (name, lbm_params overrides, expected lbm_kernel_config entries)
+CONFIGS = [
+    ("autotuned", {}, {}),
+    ("tma_12rows_2stages_512threads_slot5760_popmajor",
+     dict(kernel=2, tile_rows=12, stages=2, threads=512, layout=1),
+     dict(kind=2, tile_rows=12, stages=2, threads=512, slot_bytes=5760, layout=1, blocks_per_sm=1)),
+    ("tma_12rows_2stages_512threads_slot5760_interleaved",
+     dict(kernel=2, tile_rows=12, stages=2, threads=512, layout=2),
+     dict(kind=2, tile_rows=12, stages=2, threads=512, slot_bytes=5760, layout=2, blocks_per_sm=1)),
+    ("tma_4rows_3stages_256threads_runtime_stride_two_blocks",
+     dict(kernel=2, tile_rows=4, stages=3, threads=256, tma_slots=1),
+     dict(kind=2, tile_rows=4, stages=3, threads=256, slot_bytes=0, blocks_per_sm=2)),
+]
+
+
+@pytest.mark.parametrize("name,over,expect", CONFIGS, ids=[c[0] for c in CONFIGS])
+def test_100_cubed_les_matches_oracle(gpu_lib, les_reference, name, over, expect):
+    lbm = gpu_lib
+    u, nu0, F0, want = les_reference
+    p = lbm.make_params(N, nu0=nu0, cs=C, f0=F0, force_mode=lbm.LBM_FORCE_PAPER_SIN, **over)
+    with lbm.Lattice(p) as L:
+        cfg = L.config()
+        for k, v in expect.items():
+            assert cfg[k] == v, (name, cfg)
+        L.init(lbm.LBM_INIT_VELOCITY, u=u)
+        L.step(STEPS)
+        L.sync()
+        got = L.populations()
+    err = full_f_rel_error(got, want)
+    assert err <= 1e-5, (name, cfg, err)

@@ -59,31 +59,33 @@ def _sample_cells(rng, n, k):
     return rng.integers(0, n, size=(k, 3))  # (x, y, z)
 
 
-@pytest.mark.parametrize("precision", [0, 1, 2])
-def test_800_cubed_sampled_cells_match_oracle(gpu_lib, precision):
+@pytest.mark.parametrize("precision,C", [(0, 0.0), (1, 0.0), (2, 0.0), (0, 0.13), (1, 0.13)])
+def test_800_cubed_sampled_cells_match_oracle(gpu_lib, precision, C):
+    """C = 0: the DNS shape the bench times.  C = 0.13: the Smagorinsky branch
+    (strain, eddy viscosity, local shear rate) at the same size, the cells
+    sampled in four z planes whose theta = tau_e - 1/2 is read before each step
+    with lbm_get_theta_slice and compared with the theta of the oracle's
+    collision of the same cell."""
     import torch
-
-    import synthetic
 
     lbm = gpu_lib
     dev = torch.device("cuda", 0)
     nu0 = U0 * N / RE
     F0 = CF * U0 * U0 / N
-    k, a = synthetic.spectrum_coefficients(N, N, N, seed=1, k0=4.0, urms=0.05)
-    u = synthetic.synthesize_torch(k, a, N, N, N, dev, zchunk=32)
-    p = lbm.make_params(N, precision=precision, nu0=nu0, cs=0.0, f0=F0,
+    p = lbm.make_params(N, precision=precision, nu0=nu0, cs=C, f0=F0,
                         force_mode=lbm.LBM_FORCE_PAPER_SIN)
     c, w = oracle.lattice()
     opp = [1, 0, 3, 2, 5, 4, 7, 6, 9, 8, 11, 10, 13, 12, 15, 14, 17, 16, 18]
     rng = np.random.default_rng(2024)
     cells = _sample_cells(rng, N, 2048)
+    planes = [0, 317, 511, N - 1]
+    if C > 0:
+        cells[:, 2] = np.array(planes)[np.arange(len(cells)) % len(planes)]
     xs = np.arange(N)
     Fx = F0 * np.sin(2 * np.pi * xs / N)  # Fx(y), Fy(z), Fz(x) share this table
     try:
         with lbm.Lattice(p) as L:
-            L.init(lbm.LBM_INIT_VELOCITY, u=u)
-            del u
-            torch.cuda.empty_cache()
+            L.init_random(seed=1, urms=0.05, k0=4.0)  # the bench's workload field
             L.step(2)
             L.sync()
             A = _populations_view(torch, lbm, L, dev, ["<f4", "<f2", "bf16"][precision])
@@ -102,6 +104,8 @@ def test_800_cubed_sampled_cells_match_oracle(gpu_lib, precision):
                         ys_ = (Y - int(c[q][1])) % N
                         zs_ = (Z - int(c[q][2])) % N
                         pre[q] = A[sm[opp[q]], zs_, ys_, xs_].double()
+                # theta of the state the step collides (read-only statistics pass)
+                theta_pre = {z: lbm.lbm_get_theta_slice(L.h, 0, 2, z, (N, N, N)) for z in planes} if C > 0 else {}
                 L.step(1)
                 L.sync()
                 post = torch.empty_like(pre)
@@ -116,9 +120,14 @@ def test_800_cubed_sampled_cells_match_oracle(gpu_lib, precision):
                 pre_h = pre.cpu().numpy()
                 post_h = post.cpu().numpy()
                 want = np.empty_like(post_h)
+                theta_want = np.empty(len(cells))
                 for i, (x, y, z) in enumerate(cells):
                     F = (Fx[y], Fx[z], Fx[x])
-                    want[:, i], _ = oracle.collide_one(pre_h[:, i], F, nu0, 0.0)
+                    want[:, i], theta_want[i] = oracle.collide_one(pre_h[:, i], F, nu0, C)
+                if C > 0:
+                    theta_got = np.array([theta_pre[z][y, x] for (x, y, z) in cells])
+                    assert np.all(np.abs(theta_got - theta_want) <= 1e-5 * theta_want), parity
+                    assert theta_want.max() > 1.1 * 3 * nu0  # the eddy viscosity is active
                 if precision == 0:
                     rel = np.abs(post_h - want) / (want + w[:, None])
                     assert rel.max() <= 1e-5, (parity, rel.max())
@@ -138,19 +147,13 @@ def test_800_cubed_mass_conservation(gpu_lib):
     bench's warm-up and a few steps equals the initial sum to FP32 round-off."""
     import torch
 
-    import synthetic
-
     lbm = gpu_lib
     dev = torch.device("cuda", 0)
     nu0 = U0 * N / RE
-    k, a = synthetic.spectrum_coefficients(N, N, N, seed=1, k0=4.0, urms=0.05)
-    u = synthetic.synthesize_torch(k, a, N, N, N, dev, zchunk=32)
     p = lbm.make_params(N, nu0=nu0, cs=0.0, f0=CF * U0 * U0 / N, force_mode=lbm.LBM_FORCE_PAPER_SIN)
     try:
         with lbm.Lattice(p) as L:
-            L.init(lbm.LBM_INIT_VELOCITY, u=u)
-            del u
-            torch.cuda.empty_cache()
+            L.init_random(seed=1, urms=0.05, k0=4.0)
             A = _populations_view(torch, lbm, L, dev, "<f4")
 
             def mass():
