@@ -265,6 +265,10 @@ def lbm_init_field(h, inst: int, mode: int, amplitude: float = 0.0, u=None) -> N
         if where is not None:
             if u.dtype not in (torch.float64, torch.float32) or not u.is_contiguous():
                 raise ValueError("velocity tensor must be a contiguous float64 or float32 tensor")
+            if u.is_cuda:
+                # the handle's stream does not wait for torch's: the field must be
+                # complete before the initialisation kernel reads it
+                torch.cuda.current_stream(u.device).synchronize()
             call(ctypes.c_void_p(u.data_ptr()), where, u.dtype == torch.float32)
             return
         u = u.numpy()

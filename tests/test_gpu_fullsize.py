@@ -127,7 +127,8 @@ def test_800_cubed_sampled_cells_match_oracle(gpu_lib, precision, C):
                 if C > 0:
                     theta_got = np.array([theta_pre[z][y, x] for (x, y, z) in cells])
                     assert np.all(np.abs(theta_got - theta_want) <= 1e-5 * theta_want), parity
-                    assert theta_want.max() > 1.1 * 3 * nu0  # the eddy viscosity is active
+                    # the eddy viscosity is active (the 800^3 field is smooth: a few percent)
+                    assert theta_want.max() > 1.02 * 3 * nu0
                 if precision == 0:
                     rel = np.abs(post_h - want) / (want + w[:, None])
                     assert rel.max() <= 1e-5, (parity, rel.max())
