@@ -515,46 +515,46 @@ def les_c2_run(lbm, device, stream, n=100, steps=20000, every=500, plane=50):
     """The paper's LES workload as one job (Sec. 3.1, Sec. 4.1): n^3, C = 0.13,
     nu0 from Re = 2e4, the paper's forcing, from the seeded random field,
     `steps` steps with the statistics cadence of the paper's post-processing
-    ("computed on the fly at set intervals"): every `every` steps a fused
-    statistics record (lbm_params.stats_every), the domain statistics with the
-    derived scales and the structure functions / flatness (lbm_stats), the
-    energy spectrum (lbm_spectrum) and a theta = tau_e - 1/2 slice at
-    z = `plane` (the K_t map, lbm_get_theta_slice).  Wall time of the whole job
-    with that cadence against the same steps without it; late-time theta
-    statistics (t >= steps / 2) beside the values the paper prints for its
-    100^3 LES (Sec. 4.1: mean ~1.34e-3, 5th percentile > 1.0e-3, 95th <~
-    1.82e-3, maxima up to ~3.7e-3), context only: the paper's statistics are
-    over t/t0 in [200, 600] of a stationary state, this run starts from the
-    synthetic field."""
+    ("computed on the fly at set intervals"): every `every` steps the library's
+    statistics time series (paper_2512_23116_gb300.series: the domain
+    statistics with the derived scales and S_p / F4 by separation, the shell
+    spectrum, and a theta = tau_e - 1/2 slice at z = `plane`, the K_t map)
+    written as JSON lines, with the fused in-step records
+    (lbm_params.stats_every) besides.  Wall time of the whole job with that
+    cadence against the same steps without it; late-time theta statistics
+    (t >= steps / 2) beside the values the paper prints for its 100^3 LES
+    (Sec. 4.1: mean ~1.34e-3, 5th percentile > 1.0e-3, 95th <~ 1.82e-3, maxima
+    up to ~3.7e-3), context only: the paper's statistics are over t/t0 in
+    [200, 600] of a stationary state, this run starts from the synthetic
+    field."""
+    import tempfile
+
     import torch
-    kmax = max_shell(n, n, n)
+    from paper_2512_23116_gb300 import series
     nu0 = U0 * n / RE
 
     def params(stats_every):
         return lbm.make_params(n, nu0=nu0, cs=0.13, f0=CF * U0 * U0 / n, force_mode=lbm.LBM_FORCE_PAPER_SIN,
                                device=device, stream=stream.cuda_stream, stats_every=stats_every)
 
-    late = []
-    with lbm.Lattice(params(every)) as L:
-        L.init_random(seed=SEED, urms=URMS, k0=K0)
-        L.sync()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        nrec = 0
-        while L.time < steps:
-            L.step(every)
-            st = L.stats(what=lbm.LBM_STATS_SPECTRUM | lbm.LBM_STATS_STRUCTURE)
-            E = L.spectrum(kmax)
-            sl = L.theta_slice(2, plane)
-            nrec += 1
-            if L.time >= steps // 2:
-                late.append((st["theta_mean"], st["theta_p05"], st["theta_p50"], st["theta_p95"],
-                             st["theta_p99"], st["theta_max"], float(sl.mean()), float(sl.max()),
-                             st["F4"][0], st["Re_lambda"], st["E_k"]))
-        records = L.series()
-        wall_cadence = time.perf_counter() - t0
-        final = {"E_k": st["E_k"], "Re_lambda": st["Re_lambda"], "eta": st["eta"], "L": st["L"],
-                 "F4_r1": float(st["F4"][0]), "E": [float(f"{v:.4e}") for v in E]}
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "c2_series.jsonl")
+        with lbm.Lattice(params(every)) as L:
+            L.init_random(seed=SEED, urms=URMS, k0=K0)
+            L.sync()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            recs = series.run_with_statistics(L, steps, every, path, theta_slice=(2, plane))
+            fused = L.series()
+            wall_cadence = time.perf_counter() - t0
+        lines = len(series.read_series(path))
+        late = []
+        for r in recs:
+            if r["step"] >= steps // 2:
+                sl = np.load(os.path.join(tmp, r["theta_slice"]["file"]))
+                late.append((r["theta_mean"], r["theta_p05"], r["theta_p50"], r["theta_p95"], r["theta_p99"],
+                             r["theta_max"], float(sl.mean()), float(sl.max()), r["F4"][0], r["Re_lambda"],
+                             r["E_k"]))
     with lbm.Lattice(params(0)) as L:
         L.init_random(seed=SEED, urms=URMS, k0=K0)
         L.sync()
@@ -564,11 +564,12 @@ def les_c2_run(lbm, device, stream, n=100, steps=20000, every=500, plane=50):
         L.sync()
         wall_plain = time.perf_counter() - t0
         cfg = L.config()
+    last = recs[-1]
     a = np.array(late)
     names = ("theta_mean", "theta_p05", "theta_p50", "theta_p95", "theta_p99", "theta_max",
              "slice_theta_mean", "slice_theta_max", "F4_r1", "Re_lambda", "E_k")
     return {"n": n, "steps": steps, "every": every, "C": 0.13, "nu0": nu0, "theta_molecular_3nu0": 3 * nu0,
-            "records": nrec, "fused_records": len(records),
+            "records": len(recs), "jsonl_lines": lines, "fused_records": len(fused),
             "wall_s_with_statistics_cadence": wall_cadence, "wall_s_steps_only": wall_plain,
             "MLUPS_with_cadence": n ** 3 * steps / wall_cadence / 1e6,
             "MLUPS_steps_only": n ** 3 * steps / wall_plain / 1e6,
@@ -577,7 +578,9 @@ def les_c2_run(lbm, device, stream, n=100, steps=20000, every=500, plane=50):
             "late_time_max_theta": float(a[:, 5].max()),
             "paper_context_sec_4_1": {"theta_mean": 1.34e-3, "theta_p05_above": 1.0e-3,
                                       "theta_p95_below": 1.82e-3, "theta_max_up_to": 3.68e-3},
-            "final": final, "kernel": cfg}
+            "final": {"E_k": last["E_k"], "Re_lambda": last["Re_lambda"], "eta": last["eta"], "L": last["L"],
+                      "F4_r1": last["F4"][0], "E": [float(f"{v:.4e}") for v in last["E"]]},
+            "kernel": cfg}
 
 
 def l2_copy_rate(device, stream, mbytes=76, reps=50, rounds=4):

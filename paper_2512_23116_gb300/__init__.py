@@ -119,18 +119,22 @@ _D = ctypes.POINTER(ctypes.c_double)
 
 
 def library_path() -> str:
-    return _build.LIB
+    """liblbm_gb300.so, or its bounds-checked build when the environment sets
+    LBM_LIBRARY=checked."""
+    return _build.LIB_CHECKED if os.environ.get("LBM_LIBRARY") == "checked" else _build.LIB
 
 
 def load():
-    """Load liblbm_gb300.so; raises if it has not been built (no fallback)."""
+    """Load the library (library_path()); raises if it has not been built (no
+    fallback)."""
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(_build.LIB):
-        raise RuntimeError(f"{_build.LIB} is missing: build it with __graft_entry__.build() "
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
                            "(nvcc, sm_103a); there is no CPU fallback")
-    lib = ctypes.CDLL(_build.LIB)
+    lib = ctypes.CDLL(path)
     H = ctypes.c_void_p
     i32, i64 = ctypes.c_int32, ctypes.c_int64
     sig = {

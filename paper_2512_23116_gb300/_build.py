@@ -4,6 +4,11 @@ Each translation unit under csrc/ is compiled by nvcc in parallel with
 ``-gencode arch=compute_103a,code=sm_103a``; the objects are linked into one
 shared library with the static CUDA runtime and cuFFT.  Only the ``lbm_*``
 symbols of include/lbm.h are exported.
+
+The same sources are also built with ``-DLBM_BOUNDS_CHECK`` into
+liblbm_gb300_checked.so: every device index is checked and a failed check is
+reported as an error instead of being performed (the stand-in for a device
+memory checker; the binding loads it when LBM_LIBRARY=checked).
 """
 from __future__ import annotations
 
@@ -18,6 +23,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "liblbm_gb300.so")
+LIB_CHECKED = os.path.join(HERE, "liblbm_gb300_checked.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -53,19 +59,29 @@ def _digest() -> str:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    stamp = LIB + ".stamp"
+    """Build liblbm_gb300.so and liblbm_gb300_checked.so (when their sources
+    changed); returns the path of the first."""
+    variants = [(LIB, []), (LIB_CHECKED, ["-DLBM_BOUNDS_CHECK"])]
     dig = _digest()
-    if not force and os.path.exists(LIB) and os.path.exists(stamp):
-        with open(stamp) as fh:
-            if fh.read().strip() == dig:
-                return LIB
+    todo = []
+    for lib, defs in variants:
+        stamp = lib + ".stamp"
+        if not force and os.path.exists(lib) and os.path.exists(stamp):
+            with open(stamp) as fh:
+                if fh.read().strip() == dig:
+                    continue
+        todo.append((lib, defs))
+    if not todo:
+        return LIB
     nvcc = _nvcc()
-    os.makedirs(BUILD_DIR, exist_ok=True)
     srcs = _sources()
 
-    def compile_one(src):
-        obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+    def compile_one(job):
+        src, tag, defs = job
+        out_dir = os.path.join(BUILD_DIR, tag)
+        os.makedirs(out_dir, exist_ok=True)
+        obj = os.path.join(out_dir, os.path.basename(src) + ".o")
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *defs, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
@@ -73,17 +89,20 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static", "-lcufft",
-           "-Xlinker", "--exclude-libs,ALL"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    with open(stamp, "w") as fh:
-        fh.write(dig)
+    jobs = [(src, os.path.basename(lib).replace(".so", ""), defs) for lib, defs in todo for src in srcs]
+    with cf.ThreadPoolExecutor(max_workers=min(max(1, os.cpu_count() or 1), len(jobs), 16)) as ex:
+        objs = list(ex.map(compile_one, jobs))
+    for k, (lib, _) in enumerate(todo):
+        mine = objs[k * len(srcs):(k + 1) * len(srcs)]
+        tmp = lib + f".tmp{os.getpid()}"
+        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *mine, "-cudart", "static", "-lcufft",
+               "-Xlinker", "--exclude-libs,ALL"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stderr}")
+        os.replace(tmp, lib)
+        with open(lib + ".stamp", "w") as fh:
+            fh.write(dig)
     return LIB
 
 

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "../../include/lbm.h"
+#include "lbm_check.cuh"
 #include "lbm_internal.h"
 #include "lbm_kernels.h"
 
@@ -55,6 +56,11 @@ struct Inst {
   cufftHandle plan = 0;
   void* fft_out = nullptr;
   uint64_t rec_read = 0;
+  // what the diagnostic buffers hold: u of state version u_version; the
+  // spectrum (shells 0..spec_kmax) of state version spec_version
+  uint64_t u_version = 0, spec_version = 0;
+  int spec_kmax = -1;
+  std::vector<double> spec_E;
 };
 
 struct GraphKey {
@@ -77,6 +83,7 @@ struct lbm_s {
   std::vector<InstDesc> h_desc;
   int64_t total_tiles = 0;
   int64_t t = 0;
+  uint64_t version = 1;  // bumped by every call that changes the populations
   // kernel configuration
   int kind = 1, rows_fixed = 0, stages = 0, threads = 256, bps = 1, grid = 1, smem = 0;
   int slot_bytes = 0;  // TMA shared-memory slot layout (kSlot3, kSlot2) or 0
@@ -298,6 +305,7 @@ int build_tiles(lbm_t h) {
     d.tiles_per_plane = tpp;
     d.tile_begin = I.tile_begin;
     d.tile_end = I.tile_end;
+    d.f_elems = (int64_t)(I.f_bytes / h->esize);
   }
   h->total_tiles = tile;
   CK(h, cudaMemcpyAsync(h->d_desc, h->h_desc.data(), sizeof(InstDesc) * h->h_desc.size(),
@@ -379,6 +387,7 @@ int64_t schedule_period(lbm_t h) {
 }
 
 int run_steps(lbm_t h, int64_t n) {
+  if (n > 0) ++h->version;
   int64_t done = 0;
   const int64_t chunk = 32;
   while (done < n) {
@@ -426,6 +435,10 @@ int check_err(lbm_t h) {
   uint32_t e = 0;
   CK(h, cudaMemcpyAsync(&e, h->d_err, sizeof e, cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
+  if (kBoundsCheck) {
+    const uint32_t b = bounds_word_tma() | bounds_word_direct() | bounds_word_aux() | bounds_word_random();
+    if (b) return fail(h, LBM_ERR_CUDA, "device bounds check failed (checked build; word %u)", b);
+  }
   if (e) {
     CK(h, cudaMemsetAsync(h->d_err, 0, sizeof(uint32_t), h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
@@ -507,6 +520,7 @@ int diag_pass(lbm_t h, int i, bool want_u, bool want_aux, int plane_axis, int pl
   }
   CK(h, launch_finish(h->d_partials, (int)h->inst.size(), grid, h->d_results, nullptr, nullptr, 0, h->d_err,
                       h->stream));
+  if (want_u) I.u_version = h->version;
   return LBM_OK;
 }
 
@@ -567,6 +581,10 @@ int max_shell(int nx, int ny, int nz) {
 int spectrum_device(lbm_t h, int i, int kmax, double* host_E) {
   Inst& I = h->inst[i];
   const lbm_params& p = I.p;
+  if (I.spec_version == h->version && I.spec_kmax >= kmax) {  // this state's spectrum is at hand
+    std::copy(I.spec_E.begin(), I.spec_E.begin() + kmax + 1, host_E);
+    return LBM_OK;
+  }
   if (!I.has_plan) {
     CKF(h, cufftPlan3d(&I.plan, p.nz, p.ny, p.nx, CUFFT_R2C));
     I.has_plan = true;
@@ -590,6 +608,9 @@ int spectrum_device(lbm_t h, int i, int kmax, double* host_E) {
   CK(h, launch_spec_finish(h->d_spec, blocks, kmax, Edev, h->stream));
   CK(h, cudaMemcpyAsync(host_E, Edev, sizeof(double) * (kmax + 1), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
+  I.spec_E.assign(host_E, host_E + kmax + 1);
+  I.spec_kmax = kmax;
+  I.spec_version = h->version;
   return LBM_OK;
 }
 
@@ -937,8 +958,10 @@ LBM_API int lbm_count(lbm_t h) { return h ? (int)h->inst.size() : 0; }
 
 namespace {
 
-// A handle with one instance restarts its clock at an initialisation.
+// A handle with one instance restarts its clock at an initialisation (which
+// changes the state: every caller of reset_time initialises).
 int reset_time(lbm_t h) {
+  ++h->version;
   if (h->inst.size() == 1 && h->t != 0) {
     h->t = 0;
     h->rec_steps.clear();
@@ -1144,8 +1167,10 @@ LBM_API int lbm_stats(lbm_t h, int32_t inst, int32_t what, lbm_stats_t* out) {
   if (what & LBM_STATS_STRUCTURE) {
     std::vector<int> rs = separations(std::min({p.nx, p.ny, p.nz}));
     if ((int)rs.size() > LBM_MAX_R) rs.resize(LBM_MAX_R);
+    out->nr = 0;
+    if (rs.empty()) return LBM_OK;
     const int blocks = std::min(2 * h->num_sms, 1024);
-    const size_t need = (size_t)blocks * 6 + 6;
+    const size_t need = ((size_t)blocks + 1) * 6 * rs.size();
     if (need > h->spec_elems) {
       if (h->d_spec) cudaFree(h->d_spec);
       h->d_spec = nullptr;
@@ -1153,14 +1178,19 @@ LBM_API int lbm_stats(lbm_t h, int32_t inst, int32_t what, lbm_stats_t* out) {
       h->spec_elems = need;
     }
     out->nr = (int)rs.size();
+    // every separation into its own columns of one [blocks][nr x 6] table, one
+    // column sum, one read-back
+    const int cols = 6 * (int)rs.size();
+    for (size_t k = 0; k < rs.size(); ++k)
+      CK(h, launch_struct(I.u, p.nx, p.ny, p.nz, rs[k], h->d_spec + 6 * k, blocks, h->stream, cols));
+    CK(h, launch_sum_cols(h->d_spec, blocks, cols, h->d_spec + (size_t)blocks * cols, h->stream));
+    std::vector<double> sp(cols);
+    CK(h, cudaMemcpyAsync(sp.data(), h->d_spec + (size_t)blocks * cols, sizeof(double) * cols,
+                          cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
     for (size_t k = 0; k < rs.size(); ++k) {
-      CK(h, launch_struct(I.u, p.nx, p.ny, p.nz, rs[k], h->d_spec, blocks, h->stream));
-      CK(h, launch_sum_cols(h->d_spec, blocks, 6, h->d_spec + (size_t)blocks * 6, h->stream));
-      double sp[6];
-      CK(h, cudaMemcpyAsync(sp, h->d_spec + (size_t)blocks * 6, sizeof sp, cudaMemcpyDeviceToHost, h->stream));
-      CK(h, cudaStreamSynchronize(h->stream));
       out->r[k] = rs[k];
-      for (int q = 0; q < 6; ++q) out->Sp[k][q] = sp[q] / (3.0 * (double)I.ncell);
+      for (int q = 0; q < 6; ++q) out->Sp[k][q] = sp[6 * k + q] / (3.0 * (double)I.ncell);
       out->F4[k] = out->Sp[k][3] / (out->Sp[k][1] * out->Sp[k][1]);  // Eq. (flatness)
     }
   }
@@ -1237,8 +1267,11 @@ LBM_API int lbm_spectrum(lbm_t h, int32_t inst, double* E, int32_t kmax) {
   const lbm_params& p = h->inst[inst].p;
   const int smax = max_shell(p.nx, p.ny, p.nz);  // shells beyond hold no mode
   for (int s = smax + 1; s <= kmax; ++s) E[s] = 0.0;
-  int rc = diag_pass(h, inst, true, false, -1, 0, false);
-  if (rc != LBM_OK) return rc;
+  int rc = LBM_OK;
+  if (h->inst[inst].u_version != h->version) {  // the velocity of this state is not at hand
+    rc = diag_pass(h, inst, true, false, -1, 0, false);
+    if (rc != LBM_OK) return rc;
+  }
   rc = spectrum_device(h, inst, std::min(kmax, smax), E);
   if (rc != LBM_OK) return rc;
   return check_err(h);
@@ -1281,6 +1314,7 @@ LBM_API int lbm_set_populations(lbm_t h, int32_t inst, const double* host, int32
   CHECK_INST(h, inst);
   if (!host) return fail(h, LBM_ERR_INVALID_ARG, "null input");
   DevGuard g(h->device);
+  ++h->version;
   Inst& I = h->inst[inst];
   const int64_t chunk = std::min<int64_t>(I.ncell, kChunkCells);
   int rc = ensure_scratch(h, sizeof(double) * (size_t)chunk);
@@ -1301,6 +1335,7 @@ LBM_API int lbm_set_time(lbm_t h, int64_t t) {
   if (!h) return fail(nullptr, LBM_ERR_INVALID_ARG, "null handle");
   if (t < 0) return fail(h, LBM_ERR_INVALID_ARG, "t < 0");
   DevGuard g(h->device);
+  ++h->version;
   if ((t & 1) != (h->t & 1)) {
     size_t plane = 0;
     for (const Inst& I : h->inst) plane = std::max(plane, (size_t)I.p.nz * I.p.ny * I.nxp * h->esize);

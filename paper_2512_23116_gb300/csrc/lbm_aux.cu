@@ -73,7 +73,10 @@ __global__ void k_init(InstDesc d, bool odd, int mode, double amp, const U* __re
     float f[19];
     equilibrium((float)drho, (float)ux, (float)uy, (float)uz, f);
 #pragma unroll
-    for (int a = 0; a < 19; ++a) fb[canon_index(d, a, odd, x, y, z)] = Storage<T>::pack(f[a]);
+    for (int a = 0; a < 19; ++a) {
+      const int64_t i = canon_index(d, a, odd, x, y, z);
+      if (in_bounds(i >= 0 && i < d.f_elems)) fb[i] = Storage<T>::pack(f[a]);
+    }
   }
 }
 
@@ -86,7 +89,8 @@ __global__ void k_get_pop(InstDesc d, bool odd, int a, double* __restrict__ out,
        k += (int64_t)gridDim.x * blockDim.x) {
     int x, y, z;
     cell_xyz(c0 + k, d.nx, d.ny, x, y, z);
-    out[k] = (double)Storage<T>::cvt(fb[canon_index(d, a, odd, x, y, z)]) + w;
+    const int64_t i = canon_index(d, a, odd, x, y, z);
+    out[k] = (in_bounds(i >= 0 && i < d.f_elems) ? (double)Storage<T>::cvt(fb[i]) : 0.0) + w;
   }
 }
 
@@ -99,7 +103,8 @@ __global__ void k_set_pop(InstDesc d, bool odd, int a, const double* __restrict_
        k += (int64_t)gridDim.x * blockDim.x) {
     int x, y, z;
     cell_xyz(c0 + k, d.nx, d.ny, x, y, z);
-    fb[canon_index(d, a, odd, x, y, z)] = Storage<T>::pack((float)(in[k] - w));
+    const int64_t i = canon_index(d, a, odd, x, y, z);
+    if (in_bounds(i >= 0 && i < d.f_elems)) fb[i] = Storage<T>::pack((float)(in[k] - w));
   }
 }
 
@@ -134,8 +139,9 @@ __global__ void k_relayout(InstDesc d, bool from_odd, int a, const T* __restrict
       fbv = Storage<T>::cvt(sa[cell_off(xq, yq, zq, d.ny, d.nxp)]);
     }
     const bool to_odd = !from_odd;
-    fb[canon_index(d, a, to_odd, x, y, z)] = Storage<T>::pack((float)fa);
-    fb[canon_index(d, b, to_odd, x, y, z)] = Storage<T>::pack((float)fbv);
+    const int64_t ia = canon_index(d, a, to_odd, x, y, z), ib = canon_index(d, b, to_odd, x, y, z);
+    if (in_bounds(ia >= 0 && ia < d.f_elems)) fb[ia] = Storage<T>::pack((float)fa);
+    if (in_bounds(ib >= 0 && ib < d.f_elems)) fb[ib] = Storage<T>::pack((float)fbv);
   }
 }
 
@@ -210,7 +216,7 @@ __global__ void k_sum_cols(const double* __restrict__ p, int rows, int cols, dou
 }
 
 __global__ void k_struct(const float* __restrict__ u, int nx, int ny, int nz, int r,
-                         double* __restrict__ partials) {
+                         double* __restrict__ partials, int64_t block_stride) {
   const int64_t n = (int64_t)nx * ny * nz;
   double acc[6] = {0, 0, 0, 0, 0, 0};
   const int rx = r % nx, ry = r % ny, rz = r % nz;
@@ -221,6 +227,7 @@ __global__ void k_struct(const float* __restrict__ u, int nx, int ny, int nz, in
     const int xr = x + rx >= nx ? x + rx - nx : x + rx;
     const int yr = y + ry >= ny ? y + ry - ny : y + ry;
     const int zr = z + rz >= nz ? z + rz - nz : z + rz;
+    if (!in_bounds(xr >= 0 && xr < nx && yr >= 0 && yr < ny && zr >= 0 && zr < nz)) continue;
     const double d3[3] = {
         (double)u[((int64_t)z * ny + y) * nx + xr] - (double)u[i],
         (double)u[n + ((int64_t)z * ny + yr) * nx + x] - (double)u[n + i],
@@ -247,7 +254,7 @@ __global__ void k_struct(const float* __restrict__ u, int nx, int ny, int nz, in
   if (threadIdx.x < 6) {
     double v = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][threadIdx.x];
-    partials[(int64_t)blockIdx.x * 6 + threadIdx.x] = v;
+    partials[(int64_t)blockIdx.x * block_stride + threadIdx.x] = v;
   }
 }
 
@@ -366,8 +373,10 @@ cudaError_t launch_sum_cols(const double* partials, int rows, int cols, double* 
 }
 
 cudaError_t launch_struct(const float* u, int nx, int ny, int nz, int r, double* partials,
-                          int blocks, cudaStream_t st) {
-  return launch_kernel(k_struct, blocks, kAuxThreads, 0, st, u, nx, ny, nz, r, partials);
+                          int blocks, cudaStream_t st, int64_t block_stride) {
+  return launch_kernel(k_struct, blocks, kAuxThreads, 0, st, u, nx, ny, nz, r, partials, block_stride);
 }
+
+uint32_t bounds_word_aux() { return take_bounds_word(); }
 
 }  // namespace lbm

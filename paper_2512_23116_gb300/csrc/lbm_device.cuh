@@ -18,6 +18,7 @@
 #include <cuda_fp16.h>
 #include <cstdint>
 
+#include "lbm_check.cuh"
 #include "lbm_internal.h"
 
 namespace lbm {

@@ -30,6 +30,7 @@ struct InstDesc {
   int32_t tiles_per_plane; // ceil(ny / rows)
   int64_t tile_begin;      // first global tile of the instance
   int64_t tile_end;        // one past the last
+  int64_t f_elems;         // storage elements of the population array (bounds checks)
 };
 
 // Outputs of the read-only statistics pass (single instance).
@@ -66,6 +67,8 @@ constexpr uint32_t ERR_TIMEOUT = 2u;
 // After a timeout, loads already issued had not landed within the drain bound
 // (kDrainRounds x wait_ns) when the block left.
 constexpr uint32_t ERR_DRAIN = 4u;
+// The checked build (-DLBM_BOUNDS_CHECK) found an index outside its buffer.
+constexpr uint32_t ERR_BOUNDS = 8u;
 
 // Step kernel modes.
 enum { MODE_STEP = 0, MODE_STEP_STATS = 1, MODE_DIAG = 2 };

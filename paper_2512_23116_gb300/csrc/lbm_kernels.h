@@ -106,10 +106,11 @@ cudaError_t launch_spec_bin(const void* coeffs, int nx, int ny, int nz, int kmax
                             double* partials, int blocks, cudaStream_t st);
 cudaError_t launch_spec_finish(const double* partials, int blocks, int kmax, double* E,
                                cudaStream_t st);
-// Structure functions: partials [blocks][6] of sum over cells and axes of
-// (u_a(x + r e_a) - u_a(x))^p, p = 1..6, for velocity u [3][nz][ny][nx] FP32.
+// Structure functions: per block b, partials[b * block_stride + p - 1] = sum over
+// its cells and the three axes of (u_a(x + r e_a) - u_a(x))^p, p = 1..6, for the
+// velocity u [3][nz][ny][nx] FP32.
 cudaError_t launch_struct(const float* u, int nx, int ny, int nz, int r, double* partials,
-                          int blocks, cudaStream_t st);
+                          int blocks, cudaStream_t st, int64_t block_stride = 6);
 cudaError_t launch_sum_cols(const double* partials, int rows, int cols, double* out,
                             cudaStream_t st);
 
@@ -122,5 +123,12 @@ const char* random_velocity_f32(int nx, int ny, int nz, uint64_t seed, double ur
                                 cudaStream_t st, cudaError_t* cuda_err);
 // Largest |k| of the random field's modes: max(1, min(n_min / 2 - 1, floor(6 k0))).
 int random_field_cutoff(int nx, int ny, int nz, double k0);
+
+// Checked build (-DLBM_BOUNDS_CHECK): each kernel file's bounds word, read and
+// cleared (0 in the normal build).
+uint32_t bounds_word_tma();
+uint32_t bounds_word_direct();
+uint32_t bounds_word_aux();
+uint32_t bounds_word_random();
 
 }  // namespace lbm

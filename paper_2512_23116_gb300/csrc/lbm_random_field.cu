@@ -26,6 +26,7 @@
 #include <cmath>
 #include <vector>
 
+#include "lbm_check.cuh"
 #include "lbm_kernels.h"
 
 namespace lbm {
@@ -143,13 +144,17 @@ __global__ void k_fill_half_spectrum(uint64_t seed, int kc, int d, const double*
       const int y = ky < 0 ? ky + ny : ky, z = kz < 0 ? kz + nz : kz;
       return ((int64_t)z * ny + y) * nh + kx;
     };
+    const int64_t nU = (int64_t)nz * ny * nh;
+    auto put = [&](int64_t at, double re_, double im_) {
+      if (in_bounds(at >= 0 && at < nU)) U[at] = make_double2(re_, im_);
+    };
     if (m.kx > 0) {
-      U[slot(m.kx, m.ky, m.kz)] = make_double2(ar, ai);
+      put(slot(m.kx, m.ky, m.kz), ar, ai);
     } else if (m.kx < 0) {
-      U[slot(-m.kx, -m.ky, -m.kz)] = make_double2(ar, -ai);
+      put(slot(-m.kx, -m.ky, -m.kz), ar, -ai);
     } else {
-      U[slot(0, m.ky, m.kz)] = make_double2(ar, ai);
-      U[slot(0, -m.ky, -m.kz)] = make_double2(ar, -ai);
+      put(slot(0, m.ky, m.kz), ar, ai);
+      put(slot(0, -m.ky, -m.kz), ar, -ai);
     }
   }
 }
@@ -251,5 +256,7 @@ done:
   cudaFree(shell);
   return what;
 }
+
+uint32_t bounds_word_random() { return take_bounds_word(); }
 
 }  // namespace lbm

@@ -184,6 +184,7 @@ __device__ __forceinline__ void diag_write(const DiagOut& o, const CellDiag& g, 
                                            HistRun& run) {
   const int64_t n = (int64_t)nx * ny * nz;
   const int64_t i = ((int64_t)z * ny + y) * nx + x;
+  if (!in_bounds(x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z < nz)) return;
   if (o.u) {
     o.u[i] = g.ux;
     o.u[n + i] = g.uy;

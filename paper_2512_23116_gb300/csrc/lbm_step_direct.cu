@@ -57,7 +57,7 @@ k_step_direct(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, in
     const int ncell = rows * nx;
     T* __restrict__ fb = static_cast<T*>(d.f);
     const int zm = wrap_dec(z, nz), zp = wrap_inc(z, nz);
-    const float Fy = d.fy_of_z[z] + d.fconst[1];
+    const float Fy = (in_bounds(z >= 0 && z < nz) ? d.fy_of_z[z] : 0.f) + d.fconst[1];
     const float nu0 = d.nu0, s_nu0 = d.s_nu0, C = d.C;
     const int dr = blockDim.x / nx, dx = blockDim.x - dr * nx;  // a pass of blockDim.x cells
     int r = threadIdx.x / nx, x = threadIdx.x - r * nx;
@@ -69,32 +69,40 @@ k_step_direct(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, in
       if (!ODD) {
         const int64_t o = at(x, y, z);
 #pragma unroll
-        for (int a = 0; a < 19; ++a) f[a] = S::load(fb + slot(a) + o);
+        for (int a = 0; a < 19; ++a) {
+          const int64_t i = slot(a) + o;
+          f[a] = in_bounds(i >= 0 && i < d.f_elems) ? S::load(fb + i) : 0.f;
+        }
       } else {
 #pragma unroll
         for (int a = 0; a < 19; ++a) {
           const int xs = cx(a) > 0 ? xm : (cx(a) < 0 ? xp : x);
           const int ys = cy(a) > 0 ? ym : (cy(a) < 0 ? yp : y);
           const int zs = cz(a) > 0 ? zm : (cz(a) < 0 ? zp : z);
-          f[a] = S::load(fb + slot(opp(a)) + at(xs, ys, zs));
+          const int64_t i = slot(opp(a)) + at(xs, ys, zs);
+          f[a] = in_bounds(i >= 0 && i < d.f_elems) ? S::load(fb + i) : 0.f;
         }
       }
-      const float Fx = d.fx_of_y[y] + d.fconst[0];
-      const float Fz = d.fz_of_x[x] + d.fconst[2];
+      const float Fx = (in_bounds(y >= 0 && y < ny) ? d.fx_of_y[y] : 0.f) + d.fconst[0];
+      const float Fz = (in_bounds(x >= 0 && x < nx) ? d.fz_of_x[x] : 0.f) + d.fconst[2];
       CellDiag g;
       mrt_collide(f, Fx, Fy, Fz, nu0, s_nu0, C, g, d.strain_mode);
       if (MODE != MODE_DIAG) {
         if (!ODD) {
           const int64_t o = at(x, y, z);
 #pragma unroll
-          for (int a = 0; a < 19; ++a) fb[slot(opp(a)) + o] = S::pack(f[a]);
+          for (int a = 0; a < 19; ++a) {
+            const int64_t i = slot(opp(a)) + o;
+            if (in_bounds(i >= 0 && i < d.f_elems)) fb[i] = S::pack(f[a]);
+          }
         } else {
 #pragma unroll
           for (int a = 0; a < 19; ++a) {
             const int xd = cx(a) > 0 ? xp : (cx(a) < 0 ? xm : x);
             const int yd = cy(a) > 0 ? yp : (cy(a) < 0 ? ym : y);
             const int zd = cz(a) > 0 ? zp : (cz(a) < 0 ? zm : z);
-            fb[slot(a) + at(xd, yd, zd)] = S::pack(f[a]);
+            const int64_t i = slot(a) + at(xd, yd, zd);
+            if (in_bounds(i >= 0 && i < d.f_elems)) fb[i] = S::pack(f[a]);
           }
         }
       }
@@ -161,5 +169,7 @@ int direct_max_blocks_per_sm(int precision, int threads) {
   }
   return e == cudaSuccess ? n : 0;
 }
+
+uint32_t bounds_word_direct() { return take_bounds_word(); }
 
 }  // namespace lbm

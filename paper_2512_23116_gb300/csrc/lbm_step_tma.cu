@@ -44,6 +44,8 @@
 // histogram in shared memory when the launch reserves room for it).
 #include <cuda_runtime.h>
 
+#include <utility>
+
 #include "lbm_device.cuh"
 #include "lbm_kernels.h"
 #include "lbm_reduce.cuh"
@@ -250,11 +252,23 @@ struct SegInst {
   const void* f;
   int64_t slot_stride, plane_stride, row_stride;
   int32_t nxp, ny, nz, rows, row_copy_bytes, slot_grouped;
+  int64_t f_elems;  // checked build: storage elements of the array
 };
 
 __device__ __forceinline__ SegInst seg_inst(const InstDesc& d) {
   return SegInst{d.f, d.slot_stride, d.plane_stride, d.row_stride, d.nxp, d.ny, d.nz, d.rows,
-                 d.row_copy_bytes, d.slot_grouped};
+                 d.row_copy_bytes, d.slot_grouped, d.f_elems};
+}
+
+// Checked build: a bulk copy of `bytes` between global address g and shared
+// address s stays inside the instance's array and inside the stage [buf,
+// buf + stage_bytes).  Always true in the normal build.
+template <typename T>
+__device__ __forceinline__ bool copy_ok(const SegInst& d, const void* g, uint32_t s, uint32_t bytes, uint32_t buf,
+                                        uint32_t stage_bytes) {
+  if constexpr (!kBoundsCheck) return true;
+  return in_bounds(range_in(g, bytes, d.f, d.f_elems * (int64_t)sizeof(T)) && s >= buf &&
+                   (uint64_t)s + bytes <= (uint64_t)buf + stage_bytes);
 }
 
 template <typename T, bool ODD>
@@ -289,20 +303,25 @@ __device__ __forceinline__ SegRows seg_rows(const SegInst& d, const TileGeom& g,
 // bytes.
 template <typename T, bool ODD, int SLOT>
 __device__ __forceinline__ void load_segment(const SegInst& d, const TileGeom& g, int j, uint32_t buf,
-                                             uint32_t bar) {
+                                             uint32_t bar, uint32_t stage_bytes) {
   const uint32_t row_bytes = (uint32_t)d.nxp * (uint32_t)sizeof(T);
   const uint32_t seg_bytes = slotted<SLOT>() ? (uint32_t)SLOT : row_bytes * (uint32_t)d.rows;
   const SegRows sr = seg_rows<T, ODD>(d, g, j);
   const uint32_t pos = SLOT == kSlotGrouped ? (uint32_t)c_gpos[ODD ? c_seg_opp[j] : j] : (uint32_t)j;  // spos
   const uint32_t dst = buf + pos * seg_bytes;
   if ((uint32_t)d.row_copy_bytes == row_bytes && sr.step == (int64_t)row_bytes) {
-    bulk_load(dst, sr.plane + (int64_t)sr.ys * row_bytes, (uint32_t)sr.first * row_bytes, bar);
-    if (sr.first < g.rows)
+    const char* src = sr.plane + (int64_t)sr.ys * row_bytes;
+    if (copy_ok<T>(d, src, dst, (uint32_t)sr.first * row_bytes, buf, stage_bytes))
+      bulk_load(dst, src, (uint32_t)sr.first * row_bytes, bar);
+    if (sr.first < g.rows && copy_ok<T>(d, sr.plane, dst + (uint32_t)sr.first * row_bytes,
+                                        (uint32_t)(g.rows - sr.first) * row_bytes, buf, stage_bytes))
       bulk_load(dst + (uint32_t)sr.first * row_bytes, sr.plane, (uint32_t)(g.rows - sr.first) * row_bytes, bar);
   } else {
     for (int r = 0; r < g.rows; ++r) {
       const int y = r < sr.first ? sr.ys + r : r - sr.first;
-      bulk_load(dst + (uint32_t)r * row_bytes, sr.plane + (int64_t)y * sr.step, (uint32_t)d.row_copy_bytes, bar);
+      const char* src = sr.plane + (int64_t)y * sr.step;
+      if (copy_ok<T>(d, src, dst + (uint32_t)r * row_bytes, (uint32_t)d.row_copy_bytes, buf, stage_bytes))
+        bulk_load(dst + (uint32_t)r * row_bytes, src, (uint32_t)d.row_copy_bytes, bar);
     }
   }
 }
@@ -310,22 +329,27 @@ __device__ __forceinline__ void load_segment(const SegInst& d, const TileGeom& g
 // Producer lane j < 19: write segment j of a finished tile back to where it was
 // loaded from, as this lane's bulk async-group.
 template <typename T, bool ODD, int SLOT>
-__device__ __forceinline__ void store_segment(const SegInst& d, const TileGeom& g, int j, uint32_t buf) {
+__device__ __forceinline__ void store_segment(const SegInst& d, const TileGeom& g, int j, uint32_t buf,
+                                              uint32_t stage_bytes) {
   const uint32_t row_bytes = (uint32_t)d.nxp * (uint32_t)sizeof(T);
   const uint32_t seg_bytes = slotted<SLOT>() ? (uint32_t)SLOT : row_bytes * (uint32_t)d.rows;
   const SegRows sr = seg_rows<T, ODD>(d, g, j);
   const uint32_t pos = SLOT == kSlotGrouped ? (uint32_t)c_gpos[ODD ? c_seg_opp[j] : j] : (uint32_t)j;  // spos
   const uint32_t src = buf + pos * seg_bytes;
   if ((uint32_t)d.row_copy_bytes == row_bytes && sr.step == (int64_t)row_bytes) {
-    bulk_store(const_cast<char*>(sr.plane) + (int64_t)sr.ys * row_bytes, src, (uint32_t)sr.first * row_bytes);
-    if (sr.first < g.rows)
+    char* dst = const_cast<char*>(sr.plane) + (int64_t)sr.ys * row_bytes;
+    if (copy_ok<T>(d, dst, src, (uint32_t)sr.first * row_bytes, buf, stage_bytes))
+      bulk_store(dst, src, (uint32_t)sr.first * row_bytes);
+    if (sr.first < g.rows && copy_ok<T>(d, sr.plane, src + (uint32_t)sr.first * row_bytes,
+                                        (uint32_t)(g.rows - sr.first) * row_bytes, buf, stage_bytes))
       bulk_store(const_cast<char*>(sr.plane), src + (uint32_t)sr.first * row_bytes,
                  (uint32_t)(g.rows - sr.first) * row_bytes);
   } else {
     for (int r = 0; r < g.rows; ++r) {
       const int y = r < sr.first ? sr.ys + r : r - sr.first;
-      bulk_store(const_cast<char*>(sr.plane) + (int64_t)y * sr.step, src + (uint32_t)r * row_bytes,
-                 (uint32_t)d.row_copy_bytes);
+      char* dst = const_cast<char*>(sr.plane) + (int64_t)y * sr.step;
+      if (copy_ok<T>(d, dst, src + (uint32_t)r * row_bytes, (uint32_t)d.row_copy_bytes, buf, stage_bytes))
+        bulk_store(dst, src + (uint32_t)r * row_bytes, (uint32_t)d.row_copy_bytes);
     }
   }
   bulk_commit();
@@ -353,17 +377,21 @@ __device__ __forceinline__ const char* group_src(const SegInst& d, const TileGeo
 }
 
 template <typename T>
-__device__ __forceinline__ void load_group(const SegInst& d, const TileGeom& g, int k, uint32_t buf, uint32_t bar) {
+__device__ __forceinline__ void load_group(const SegInst& d, const TileGeom& g, int k, uint32_t buf, uint32_t bar,
+                                           uint32_t stage_bytes) {
   const uint32_t row_bytes = (uint32_t)d.nxp * (uint32_t)sizeof(T);
-  bulk_load(buf + (uint32_t)c_grp_start[k] * row_bytes, group_src<T>(d, g, k), (uint32_t)c_grp_len[k] * row_bytes,
-            bar);
+  const char* src = group_src<T>(d, g, k);
+  const uint32_t dst = buf + (uint32_t)c_grp_start[k] * row_bytes, bytes = (uint32_t)c_grp_len[k] * row_bytes;
+  if (copy_ok<T>(d, src, dst, bytes, buf, stage_bytes)) bulk_load(dst, src, bytes, bar);
 }
 
 template <typename T>
-__device__ __forceinline__ void store_group(const SegInst& d, const TileGeom& g, int k, uint32_t buf) {
+__device__ __forceinline__ void store_group(const SegInst& d, const TileGeom& g, int k, uint32_t buf,
+                                            uint32_t stage_bytes) {
   const uint32_t row_bytes = (uint32_t)d.nxp * (uint32_t)sizeof(T);
-  bulk_store(const_cast<char*>(group_src<T>(d, g, k)), buf + (uint32_t)c_grp_start[k] * row_bytes,
-             (uint32_t)c_grp_len[k] * row_bytes);
+  char* dst = const_cast<char*>(group_src<T>(d, g, k));
+  const uint32_t src = buf + (uint32_t)c_grp_start[k] * row_bytes, bytes = (uint32_t)c_grp_len[k] * row_bytes;
+  if (copy_ok<T>(d, dst, src, bytes, buf, stage_bytes)) bulk_store(dst, src, bytes);
   bulk_commit();
 }
 
@@ -371,20 +399,21 @@ __device__ __forceinline__ void store_group(const SegInst& d, const TileGeom& g,
 // group or a segment, or nothing).
 template <typename T, bool ODD, int SLOT>
 __device__ __forceinline__ void tile_load(const SegInst& d, const TileGeom& g, int lane, uint32_t buf,
-                                          uint32_t bar) {
+                                          uint32_t bar, uint32_t stage_bytes) {
   if (grouped_copies<T, ODD, SLOT>(d)) {
-    if (lane < 9) load_group<T>(d, g, lane, buf, bar);
+    if (lane < 9) load_group<T>(d, g, lane, buf, bar, stage_bytes);
   } else if (lane < 19) {
-    load_segment<T, ODD, SLOT>(d, g, lane, buf, bar);
+    load_segment<T, ODD, SLOT>(d, g, lane, buf, bar, stage_bytes);
   }
 }
 
 template <typename T, bool ODD, int SLOT>
-__device__ __forceinline__ void tile_store(const SegInst& d, const TileGeom& g, int lane, uint32_t buf) {
+__device__ __forceinline__ void tile_store(const SegInst& d, const TileGeom& g, int lane, uint32_t buf,
+                                           uint32_t stage_bytes) {
   if (grouped_copies<T, ODD, SLOT>(d)) {
-    if (lane < 9) store_group<T>(d, g, lane, buf);
+    if (lane < 9) store_group<T>(d, g, lane, buf, stage_bytes);
   } else if (lane < 19) {
-    store_segment<T, ODD, SLOT>(d, g, lane, buf);
+    store_segment<T, ODD, SLOT>(d, g, lane, buf, stage_bytes);
   }
 }
 
@@ -395,9 +424,78 @@ __device__ __forceinline__ uint32_t tile_bytes_of(const SegInst& d, const TileGe
   return 19u * per_row * (uint32_t)g.rows;
 }
 
+// Shared-memory accesses of the compile-time slot variants with the slot
+// offset in the instruction: one address register per distinct x position of
+// a cell (x, and x -+ 1 in odd steps), the population's slot offset as an
+// immediate (the compiler did not fold these offsets on its own: ~40 integer
+// instructions per cell went to addressing).  Volatile asm keeps them in
+// program order with the barrier waits and fences around them.
+template <typename T> struct SmemIO;
+template <> struct SmemIO<float> {
+  template <int OFF> static __device__ __forceinline__ float ld(uint32_t a) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(a), "n"(OFF));
+    return v;
+  }
+  template <int OFF> static __device__ __forceinline__ void st(uint32_t a, float v) {
+    asm volatile("st.shared.f32 [%0+%1], %2;" ::"r"(a), "n"(OFF), "f"(v) : "memory");
+  }
+};
+template <> struct SmemIO<__half> {
+  template <int OFF> static __device__ __forceinline__ float ld(uint32_t a) {
+    unsigned short h;
+    asm volatile("ld.shared.b16 %0, [%1+%2];" : "=h"(h) : "r"(a), "n"(OFF));
+    return __half2float(__ushort_as_half(h));
+  }
+  template <int OFF> static __device__ __forceinline__ void st(uint32_t a, float v) {
+    asm volatile("st.shared.b16 [%0+%1], %2;" ::"r"(a), "n"(OFF), "h"(__half_as_ushort(__float2half_rn(v)))
+                 : "memory");
+  }
+};
+template <> struct SmemIO<__nv_bfloat16> {
+  template <int OFF> static __device__ __forceinline__ float ld(uint32_t a) {
+    unsigned short h;
+    asm volatile("ld.shared.b16 %0, [%1+%2];" : "=h"(h) : "r"(a), "n"(OFF));
+    return __bfloat162float(__ushort_as_bfloat16(h));
+  }
+  template <int OFF> static __device__ __forceinline__ void st(uint32_t a, float v) {
+    asm volatile("st.shared.b16 [%0+%1], %2;" ::"r"(a), "n"(OFF),
+                 "h"(__bfloat16_as_ushort(__float2bfloat16_rn(v)))
+                 : "memory");
+  }
+};
+
+// f_A of a cell: segment spos(A) at x - [odd] cx_A (address bm for x - 1, bp
+// for x + 1, b0 for x).
+template <typename T, bool ODD, int SLOT, int A>
+__device__ __forceinline__ float ld_pop(uint32_t b0, uint32_t bm, uint32_t bp) {
+  constexpr int kOff = spos<SLOT>(A, ODD) * SLOT;
+  const uint32_t b = ODD ? (cx(A) > 0 ? bm : (cx(A) < 0 ? bp : b0)) : b0;
+  return SmemIO<T>::template ld<kOff>(b);
+}
+template <typename T, bool ODD, int SLOT, int... A>
+__device__ __forceinline__ void ld_pops(float (&f)[19], uint32_t b0, uint32_t bm, uint32_t bp,
+                                        std::integer_sequence<int, A...>) {
+  ((f[A] = ld_pop<T, ODD, SLOT, A>(b0, bm, bp)), ...);
+}
+// f*_A of a cell into segment spos(opp A) at x + [odd] cx_A.
+template <typename T, bool ODD, int SLOT, int A>
+__device__ __forceinline__ void st_pop(const float (&f)[19], uint32_t b0, uint32_t bm, uint32_t bp) {
+  constexpr int kOff = spos<SLOT>(opp(A), ODD) * SLOT;
+  const uint32_t b = ODD ? (cx(A) > 0 ? bp : (cx(A) < 0 ? bm : b0)) : b0;
+  SmemIO<T>::template st<kOff>(b, f[A]);
+}
+template <typename T, bool ODD, int SLOT, int... A>
+__device__ __forceinline__ void st_pops(const float (&f)[19], uint32_t b0, uint32_t bm, uint32_t bp,
+                                        std::integer_sequence<int, A...>) {
+  (st_pop<T, ODD, SLOT, A>(f, b0, bm, bp), ...);
+}
+
 // Per-instance constants of a consumer thread's cell loop.
 struct CellLoop {
   int nx, nxp;
+  int stage_elems;       // checked build: values of one stage
+  int ny;                // checked build: rows of the Fx table
   int seg;               // population stride in shared memory (values)
   int dr, dx;            // a pass of nct cells advances dr rows and dx cells
   int r0, x0;            // the thread's first cell of a tile
@@ -426,26 +524,57 @@ __device__ __forceinline__ void collide_tile(const CellLoop& cl, int ncell, cons
                                              const float* __restrict__ fz_table, int nct, Acc& acc,
                                              const DiagTile& dt, HistRun& run) {
   using S = Storage<T>;
+  // compile-time slots: immediate offsets (SmemIO); otherwise indexed accesses
+  constexpr bool kImm = slotted<SLOT>() && !kBoundsCheck;
+  using Pops = std::make_integer_sequence<int, 19>;
   const int nx = cl.nx, seg = cl.seg;
+  const uint32_t sbase = smem_addr(sbuf);
   int r = cl.r0, x = cl.x0;
   for (int c = r * nx + x; c < ncell; c += nct) {
     const int xm = wrap_dec(x, nx), xp = wrap_inc(x, nx);
     T* row = sbuf + r * cl.nxp;
+    const uint32_t b0 = sbase + (uint32_t)(r * cl.nxp + x) * (uint32_t)sizeof(T);
+    const uint32_t bm = b0 + (uint32_t)((xm - x) * (int)sizeof(T));
+    const uint32_t bp = b0 + (uint32_t)((xp - x) * (int)sizeof(T));
     float f[19];
+    if constexpr (kImm) {
+      ld_pops<T, ODD, SLOT>(f, b0, bm, bp, Pops{});
+    } else {
 #pragma unroll
-    for (int a = 0; a < 19; ++a) {
-      const int xs = ODD ? (cx(a) > 0 ? xm : (cx(a) < 0 ? xp : x)) : x;
-      f[a] = S::cvt(row[spos<SLOT>(a, ODD) * seg + xs]);
+      for (int a = 0; a < 19; ++a) {
+        const int xs = ODD ? (cx(a) > 0 ? xm : (cx(a) < 0 ? xp : x)) : x;
+        if constexpr (kBoundsCheck) {
+          const int e = r * cl.nxp + spos<SLOT>(a, ODD) * seg + xs;
+          f[a] = in_bounds(e >= 0 && e < cl.stage_elems) ? S::cvt(sbuf[e]) : 0.f;
+        } else {
+          f[a] = S::cvt(row[spos<SLOT>(a, ODD) * seg + xs]);
+        }
+      }
     }
-    const float Fx = __ldg(fx + r) + cl.fx_const;
-    const float Fz = fz_table[x];
+    float Fx, Fz;
+    if constexpr (kBoundsCheck) {
+      Fx = (in_bounds(dt.y0 + r >= 0 && dt.y0 + r < cl.ny) ? __ldg(fx + r) : 0.f) + cl.fx_const;
+      Fz = in_bounds(x >= 0 && x < nx) ? fz_table[x] : 0.f;
+    } else {
+      Fx = __ldg(fx + r) + cl.fx_const;
+      Fz = fz_table[x];
+    }
     CellDiag cd;
     mrt_collide(f, Fx, Fy, Fz, cl.nu0, cl.s_nu0, cl.C, cd, SMODE);
     if (MODE != MODE_DIAG) {
+      if constexpr (kImm) {
+        st_pops<T, ODD, SLOT>(f, b0, bm, bp, Pops{});
+      } else {
 #pragma unroll
-      for (int a = 0; a < 19; ++a) {
-        const int xd = ODD ? (cx(a) > 0 ? xp : (cx(a) < 0 ? xm : x)) : x;
-        row[spos<SLOT>(opp(a), ODD) * seg + xd] = S::pack(f[a]);
+        for (int a = 0; a < 19; ++a) {
+          const int xd = ODD ? (cx(a) > 0 ? xp : (cx(a) < 0 ? xm : x)) : x;
+          if constexpr (kBoundsCheck) {
+            const int e = r * cl.nxp + spos<SLOT>(opp(a), ODD) * seg + xd;
+            if (in_bounds(e >= 0 && e < cl.stage_elems)) sbuf[e] = S::pack(f[a]);
+          } else {
+            row[spos<SLOT>(opp(a), ODD) * seg + xd] = S::pack(f[a]);
+          }
+        }
       }
     }
     if (MODE != MODE_STEP) acc.add(cd, Fx, Fy, Fz, cl.C);
@@ -511,7 +640,7 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
         const uint32_t bar = bar_full + 8u * loaded;
         if (lane == 0) mbar_expect_tx(bar, tile_bytes_of(d, g, (int)sizeof(T)));
         __syncwarp();
-        tile_load<T, ODD, SLOT>(d, g, lane, buf0 + (uint32_t)loaded * tile_bytes, bar);
+        tile_load<T, ODD, SLOT>(d, g, lane, buf0 + (uint32_t)loaded * tile_bytes, bar, (uint32_t)tile_bytes);
       }
       walker_next(wl, insts, ninst, stride, tile_hi);
     }
@@ -537,7 +666,7 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
         sis = seg_inst(insts[g.ii]);
         sis_ii = g.ii;
       }
-      if (MODE != MODE_DIAG) tile_store<T, ODD, SLOT>(sis, g, lane, buf);
+      if (MODE != MODE_DIAG) tile_store<T, ODD, SLOT>(sis, g, lane, buf, (uint32_t)tile_bytes);
       walker_next(ws, insts, ninst, stride, tile_hi);
       if (loaded < ntiles) {
         const TileGeom gn = walker_geom(wl);
@@ -556,7 +685,7 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
         // have read the stage first
         bulk_wait_read_all();
         if (gn.ii != g.ii) __syncwarp();
-        tile_load<T, ODD, SLOT>(dn, gn, lane, buf, bar);
+        tile_load<T, ODD, SLOT>(dn, gn, lane, buf, bar, (uint32_t)tile_bytes);
         ++loaded;
       }
       if (++s == stages) {
@@ -619,6 +748,8 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
       cur = w.ii;
       cl.nx = d.nx;
       cl.nxp = d.nxp;
+      cl.ny = d.ny;
+      cl.stage_elems = tile_bytes / (int)sizeof(T);
       cl.seg = slotted<SLOT>() ? SLOT / (int)sizeof(T) : d.rows * d.nxp;
       cl.dr = nct / d.nx;
       cl.dx = nct - cl.dr * d.nx;
@@ -800,5 +931,7 @@ int tma_max_blocks_per_sm(int precision, int slot_bytes, int threads, int smem_b
   }
   return e == cudaSuccess ? n : 0;
 }
+
+uint32_t bounds_word_tma() { return take_bounds_word(); }
 
 }  // namespace lbm

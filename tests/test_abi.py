@@ -145,3 +145,12 @@ def test_batch_and_velocity_entry_points_validate_arguments(lib):
     with pytest.raises(lib.LbmError) as ei:
         lib.lbm_batch_create([a, b])
     assert ei.value.code == lib.LBM_ERR_UNSUPPORTED
+
+
+def test_series_shell_count_matches_the_oracle_rule():
+    """The series writer bins the spectrum into the same shells as the oracle."""
+    from oracle import diagnostics as dg
+    from paper_2512_23116_gb300 import series
+
+    for shape in ((24, 24, 24), (100, 100, 100), (40, 36, 32), (7, 5, 3), (800, 800, 800)):
+        assert series._max_shell(*shape) == dg.max_shell(*shape)
