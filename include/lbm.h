@@ -122,7 +122,9 @@ typedef struct lbm_params {
                              tries the runtime stride), 1 always the runtime
                              stride (x-lines of a tile packed; with one-x-line
                              tiles of the row-interleaved array an odd step
-                             copies each slot group of a cell row in one piece) */
+                             copies each slot group of a cell row in one piece),
+                             2 the compile-time slots sized for two co-resident
+                             blocks per SM (two stages of 2880-byte slots) */
 } lbm_params;
 
 /* Domain statistics of one instance at one time (all FP64 sums on the device). */

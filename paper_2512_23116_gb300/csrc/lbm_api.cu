@@ -167,7 +167,7 @@ int validate(const lbm_params& p, std::string& why) {
   if (p.tile_rows < 0) { why = "tile_rows < 0"; return LBM_ERR_INVALID_ARG; }
   if (p.strain_mode < 0 || p.strain_mode > 1) { why = "strain_mode must be 0 or 1"; return LBM_ERR_INVALID_ARG; }
   if (p.layout < 0 || p.layout > 2) { why = "layout must be 0, 1 or 2"; return LBM_ERR_INVALID_ARG; }
-  if (p.tma_slots < 0 || p.tma_slots > 1) { why = "tma_slots must be 0 or 1"; return LBM_ERR_INVALID_ARG; }
+  if (p.tma_slots < 0 || p.tma_slots > 2) { why = "tma_slots must be 0, 1 or 2"; return LBM_ERR_INVALID_ARG; }
   if (p.row_align != 0 && (p.row_align < 16 || p.row_align > 65536 || (p.row_align & (p.row_align - 1)))) {
     why = "row_align must be 0 or a power of two in [16, 65536]";
     return LBM_ERR_INVALID_ARG;
@@ -753,10 +753,12 @@ struct Candidate {
 // TMA candidate with R x-lines per tile: the compile-time slot layout when
 // the stage count has one and R x-lines of every instance fit a slot
 // (row_stage = 19 x-lines of the widest instance), else the runtime stride.
-Candidate tma_candidate(int64_t row_stage, int R, int stages, int threads, bool slots = true) {
+Candidate tma_candidate(int64_t row_stage, int R, int stages, int threads, bool slots = true,
+                        bool two_blocks = false) {
   const int64_t seg = row_stage / 19 * R;  // bytes of R x-lines of one population
-  if (slots && stages == 3 && seg <= kSlot3) return {2, threads, stages, 19 * kSlot3, R, kSlot3, 0};
-  if (slots && stages == 2 && seg <= kSlot2) return {2, threads, stages, 19 * kSlot2, R, kSlot2, 0};
+  if (slots && two_blocks && stages == 2 && seg <= kSlot2h) return {2, threads, stages, 19 * kSlot2h, R, kSlot2h, 0};
+  if (slots && !two_blocks && stages == 3 && seg <= kSlot3) return {2, threads, stages, 19 * kSlot3, R, kSlot3, 0};
+  if (slots && !two_blocks && stages == 2 && seg <= kSlot2) return {2, threads, stages, 19 * kSlot2, R, kSlot2, 0};
   return {2, threads, stages, (int)((row_stage * R + 15) / 16 * 16), R, 0, 0};
 }
 
@@ -848,7 +850,11 @@ int choose_config(lbm_t h, const lbm_params& p0) {
     return apply_candidate(h, {1, p0.threads, 0, 0, requested_rows, 0, lay_fixed});
   const bool allow_slots = p0.tma_slots == 0;
   if (requested_kind == 2 && requested_rows > 0 && p0.threads > 0 && p0.stages > 0) {
-    Candidate c = tma_candidate(row_stage, requested_rows, p0.stages, p0.threads, allow_slots);
+    Candidate c = p0.tma_slots == 2
+                      ? tma_candidate(row_stage, requested_rows, p0.stages, p0.threads, true, true)
+                      : tma_candidate(row_stage, requested_rows, p0.stages, p0.threads, allow_slots);
+    if (p0.tma_slots == 2 && c.slot_bytes != kSlot2h)
+      return fail(h, LBM_ERR_UNSUPPORTED, "tma_slots = 2 needs two stages whose tile rows fit a %d-byte slot", kSlot2h);
     if (!fits(p0.stages, c.tile_bytes)) c = tma_candidate(row_stage, requested_rows, p0.stages, p0.threads, false);
     if (!tma_ok || !fits(p0.stages, c.tile_bytes))
       return fail(h, LBM_ERR_UNSUPPORTED, "requested TMA stages do not fit shared memory");
@@ -882,14 +888,36 @@ int choose_config(lbm_t h, const lbm_params& p0) {
               r.layout = 1;
               if (fits(s, r.tile_bytes)) cands.push_back(r);
             }
-            // two co-resident blocks per SM: stages sized to the tile (runtime
-            // stride) when that leaves room for a second block, so that one
-            // block's pipeline fill and drain overlap the other's steady state
-            if (th == 256 && c.slot_bytes != 0) {
-              Candidate r = tma_candidate(row_stage, R, s, th, false);
-              r.layout = lay;
-              if (2 * (tma_smem_bytes(s, r.tile_bytes, max_nx) + 1024) <= kSmemPerSm) cands.push_back(r);
-            }
+
+          }
+        }
+      }
+    }
+    // two co-resident blocks of 256 threads per SM: stages small enough for a
+    // second block, so that one block's pipeline fill and drain overlap the
+    // other's steady state (small lattices, where each block sees few tiles
+    // per step): the largest tiles that fit, and the listed smaller ones, in
+    // the runtime stride and, with two stages, in kSlot2h slots
+    // (population-major array; the row-interleaved one only for one-x-line tiles)
+    for (int s : {2, 3}) {
+      const int64_t per_block = kSmemPerSm / 2 - 1024 - tma_smem_bytes(s, 0, max_nx);
+      const int rmax = (int)std::min<int64_t>(per_block / (s * row_stage), std::max(1, min_ny));
+      if (rmax < 1) continue;
+      std::vector<int> rs_two = {rmax};
+      for (int R : row_opts)
+        if (R < rmax) rs_two.push_back(R);
+      for (int R : rs_two) {
+        if (requested_rows > 0 && R != requested_rows) continue;
+        for (bool slot_variant : {false, true}) {
+          if (slot_variant && (s != 2 || !allow_slots)) continue;
+          Candidate c = tma_candidate(row_stage, R, s, 256, slot_variant, true);
+          if (slot_variant && c.slot_bytes != kSlot2h) continue;
+          if (2 * (tma_smem_bytes(s, c.tile_bytes, max_nx) + 1024) > kSmemPerSm) continue;
+          for (int lay = 0; lay < 2; ++lay) {
+            if ((lay_req == 1 && lay == 1) || (lay_req == 2 && lay == 0)) continue;
+            if (lay == 1 && R > 1) continue;
+            c.layout = lay;
+            cands.push_back(c);
           }
         }
       }

@@ -39,7 +39,7 @@ struct LaunchArgs {
   int grid, threads;
   // TMA kernel configuration
   int stages;
-  int slot_bytes;          // shared-memory slot per population segment: kSlot3, kSlot2, or the runtime
+  int slot_bytes;          // shared-memory slot per population segment: kSlot3, kSlot2, kSlot2h, or the runtime
                            // stride rows x nxp: 0, or kSlotGrouped for the row-interleaved array
   int smem_bytes;          // dynamic shared memory of the TMA kernel
   int tile_bytes_max;      // bytes of one stage (19 segments)
@@ -60,6 +60,9 @@ int direct_max_blocks_per_sm(int precision, int threads);
 // size) <= slot.
 constexpr int kSlot3 = 3840;
 constexpr int kSlot2 = 5760;
+// Two stages of 19 slots of kSlot2h bytes (109 KB) leave room for a second
+// co-resident block on the SM.
+constexpr int kSlot2h = 2880;
 // Runtime-stride tiles of the row-interleaved array: segments at the grouped
 // positions of their slots (odd steps then copy whole slot groups).
 constexpr int kSlotGrouped = -1;

@@ -832,6 +832,7 @@ cudaError_t dispatch_tma(const LaunchArgs& la, cudaStream_t st) {
     case kSlotGrouped: return dispatch_tma_s<T, kSlotGrouped>(la, st);
     case kSlot3: return dispatch_tma_s<T, kSlot3>(la, st);
     case kSlot2: return dispatch_tma_s<T, kSlot2>(la, st);
+    case kSlot2h: return dispatch_tma_s<T, kSlot2h>(la, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -857,6 +858,7 @@ cudaError_t set_smem(int smem) {
   if (e == cudaSuccess) e = set_smem_s<T, kSlotGrouped>(smem);
   if (e == cudaSuccess) e = set_smem_s<T, kSlot3>(smem);
   if (e == cudaSuccess) e = set_smem_s<T, kSlot2>(smem);
+  if (e == cudaSuccess) e = set_smem_s<T, kSlot2h>(smem);
   return e;
 }
 
@@ -870,6 +872,9 @@ cudaError_t occupancy(int* n, int slot_bytes, int threads, int smem_bytes) {
                                                            smem_bytes);
     case kSlot3:
       return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_step_tma<T, true, MODE, kSlot3>, threads,
+                                                           smem_bytes);
+    case kSlot2h:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_step_tma<T, true, MODE, kSlot2h>, threads,
                                                            smem_bytes);
     case kSlot2:
       return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_step_tma<T, true, MODE, kSlot2>, threads,

@@ -9,7 +9,8 @@ The configurations: what the autotuner picks (the bench's 100^3 line runs
 the autotuner), and fixed TMA configurations among its candidates, each
 asserted through lbm_kernel_config: 12 x-lines per tile with two stages of
 5760 B slots and 512 threads (one block per SM), and tiles small enough for
-two co-resident blocks per SM (256 threads)."""
+two co-resident blocks per SM (256 threads): the runtime stride with 4 and 6
+x-lines, and 7 x-lines in two stages of 2880 B slots."""
 import numpy as np
 import pytest
 
@@ -47,6 +48,12 @@ CONFIGS = [
     ("tma_4rows_3stages_256threads_runtime_stride_two_blocks",
      dict(kernel=2, tile_rows=4, stages=3, threads=256, tma_slots=1),
      dict(kind=2, tile_rows=4, stages=3, threads=256, slot_bytes=0, blocks_per_sm=2)),
+    ("tma_6rows_2stages_256threads_runtime_stride_two_blocks",
+     dict(kernel=2, tile_rows=6, stages=2, threads=256, tma_slots=1, layout=1),
+     dict(kind=2, tile_rows=6, stages=2, threads=256, slot_bytes=0, blocks_per_sm=2)),
+    ("tma_7rows_2stages_256threads_slot2880_two_blocks",
+     dict(kernel=2, tile_rows=7, stages=2, threads=256, tma_slots=2, layout=1),
+     dict(kind=2, tile_rows=7, stages=2, threads=256, slot_bytes=2880, blocks_per_sm=2)),
 ]
 
 

@@ -338,25 +338,29 @@ def test_initial_field_sources_agree(gpu_lib):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_tma_shared_memory_layouts_agree(gpu_lib, precision):
-    """The TMA kernel's three shared-memory layouts (3840 B slots with 3
-    stages, 5760 B slots with 2, the runtime stride rows x nxp with 4 stages)
+    """The TMA kernel's shared-memory layouts (3840 B slots with 3 stages,
+    5760 B slots with 2, the runtime stride rows x nxp with 4 stages, and the
+    2880 B slots with 2 stages sized for two co-resident blocks per SM)
     compute every cell identically: bitwise-equal populations after 33 steps,
     including a ragged last tile (ny = 23 with 2 x-lines per tile)."""
     lbm = gpu_lib
     nx, ny, nz = 40, 23, 12
     u = synthetic.random_solenoidal(nx, ny, nz, seed=5)
     out = []
-    for stages in (3, 2, 4):
+    for stages, slots, slot_bytes, bps in ((3, 0, 3840, 1), (2, 0, 5760, 1), (4, 0, 0, None), (2, 2, 2880, 2)):
         p = lbm.make_params(nx, ny, nz, precision=precision, nu0=0.002, cs=0.13, f0=1e-4,
                             force_mode=lbm.LBM_FORCE_PAPER_SIN, kernel=2, tile_rows=2, stages=stages,
-                            threads=256)
+                            threads=256, tma_slots=slots)
         with lbm.Lattice(p) as L:
             cfg = L.config()
-            assert (cfg["kind"], cfg["tile_rows"], cfg["stages"]) == (2, 2, stages)
+            assert (cfg["kind"], cfg["tile_rows"], cfg["stages"], cfg["slot_bytes"]) == (2, 2, stages, slot_bytes)
+            if bps is not None:
+                assert cfg["blocks_per_sm"] == bps
             L.init(lbm.LBM_INIT_VELOCITY, u=u)
             L.step(33)
             out.append(L.populations())
-    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+    for o in out[1:]:
+        assert np.array_equal(out[0], o)
 
 
 @pytest.mark.parametrize("kind", KINDS)
