@@ -258,6 +258,70 @@ __global__ void k_struct(const float* __restrict__ u, int nx, int ny, int nz, in
   }
 }
 
+// Structure functions of up to 24 separations in one launch (blockIdx.y =
+// separation): per block b and separation k, partials[(b * nr + k) * 6 + p - 1]
+// = sum over its cells and the three axes of d^p, d = u_a(x + r_k e_a) - u_a(x),
+// p = 1..6.  The powers and the running sums are FP32 (FP64 arithmetic is slow
+// on this part: with FP64 powers the 256^3 structure functions took 17 ms),
+// folded into FP64 totals every kFoldStruct cells; the block reduction is FP64.
+constexpr int kFoldStruct = 32;
+
+__global__ void k_struct_multi(const float* __restrict__ u, int nx, int ny, int nz, StructSeps seps, int nr,
+                               double* __restrict__ partials) {
+  const int k = blockIdx.y;
+  const int64_t n = (int64_t)nx * ny * nz;
+  const int r = seps.r[k];
+  const int rx = r % nx, ry = r % ny, rz = r % nz;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  float t[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  int cnt = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int x, y, z;
+    cell_xyz(i, nx, ny, x, y, z);
+    const int xr = x + rx >= nx ? x + rx - nx : x + rx;
+    const int yr = y + ry >= ny ? y + ry - ny : y + ry;
+    const int zr = z + rz >= nz ? z + rz - nz : z + rz;
+    if (!in_bounds(xr >= 0 && xr < nx && yr >= 0 && yr < ny && zr >= 0 && zr < nz)) continue;
+    const float d3[3] = {u[((int64_t)z * ny + y) * nx + xr] - u[i],
+                         u[n + ((int64_t)z * ny + yr) * nx + x] - u[n + i],
+                         u[2 * n + ((int64_t)zr * ny + y) * nx + x] - u[2 * n + i]};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float q = d3[a];
+#pragma unroll
+      for (int p = 0; p < 6; ++p) {
+        t[p] += q;
+        q *= d3[a];
+      }
+    }
+    if (++cnt == kFoldStruct) {
+#pragma unroll
+      for (int p = 0; p < 6; ++p) {
+        acc[p] += (double)t[p];
+        t[p] = 0.f;
+      }
+      cnt = 0;
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < 6; ++p) acc[p] += (double)t[p];
+  __shared__ double red[32][6];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int p = 0; p < 6; ++p) {
+    double v = acc[p];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) red[warp][p] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][threadIdx.x];
+    partials[((int64_t)blockIdx.x * nr + k) * 6 + threadIdx.x] = v;
+  }
+}
+
 int grid_for(int64_t n) {
   int64_t b = (n + kAuxThreads - 1) / kAuxThreads;
   if (b < 1) b = 1;
@@ -370,6 +434,14 @@ cudaError_t launch_spec_finish(const double* partials, int blocks, int kmax, dou
 cudaError_t launch_sum_cols(const double* partials, int rows, int cols, double* out,
                             cudaStream_t st) {
   return launch_kernel(k_sum_cols, (cols + 255) / 256, 256, 0, st, partials, rows, cols, out);
+}
+
+cudaError_t launch_struct_multi(const float* u, int nx, int ny, int nz, const int* r, int nr, double* partials,
+                                int blocks, cudaStream_t st) {
+  if (nr < 1 || nr > kMaxStructSeps) return cudaErrorInvalidValue;
+  StructSeps seps{};
+  for (int k = 0; k < nr; ++k) seps.r[k] = r[k];
+  return launch_kernel(k_struct_multi, dim3(blocks, nr), kAuxThreads, 0, st, u, nx, ny, nz, seps, nr, partials);
 }
 
 cudaError_t launch_struct(const float* u, int nx, int ny, int nz, int r, double* partials,

@@ -27,6 +27,25 @@ inline cudaError_t launch_kernel(void (*kernel)(P...), dim3 grid, dim3 block, si
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
 }
 
+// The same with programmatic dependent launch allowed: the kernel may be
+// scheduled while the previous kernel in the stream is finishing, and must
+// execute griddepcontrol.wait before it touches that kernel's results.
+template <typename... P, typename... A>
+inline cudaError_t launch_kernel_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                     A&&... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
+
 struct LaunchArgs {
   const InstDesc* insts;   // device table
   int ninst;
@@ -48,6 +67,7 @@ struct LaunchArgs {
   int withhold_first_load; // test hook: block 0 never loads its first tile
   int hist_smem;           // TMA statistics pass: byte offset of the theta histogram in
                            // dynamic shared memory (0: global counts)
+  int pdl;                 // launch with programmatic dependent launch (step kernels)
 };
 
 cudaError_t launch_step_direct(const LaunchArgs& la, cudaStream_t st);
@@ -114,6 +134,16 @@ cudaError_t launch_spec_finish(const double* partials, int blocks, int kmax, dou
 // velocity u [3][nz][ny][nx] FP32.
 cudaError_t launch_struct(const float* u, int nx, int ny, int nz, int r, double* partials,
                           int blocks, cudaStream_t st, int64_t block_stride = 6);
+// The separations of one launch (kernel parameter).
+constexpr int kMaxStructSeps = 24;
+struct StructSeps {
+  int r[kMaxStructSeps];
+};
+// Structure functions of nr <= 24 separations r[0..nr) in one launch, FP32
+// powers folded into FP64: partials [blocks][nr][6] of the per-block sums over
+// cells and the three axes of d^p, p = 1..6.
+cudaError_t launch_struct_multi(const float* u, int nx, int ny, int nz, const int* r, int nr, double* partials,
+                                int blocks, cudaStream_t st);
 cudaError_t launch_sum_cols(const double* partials, int rows, int cols, double* out,
                             cudaStream_t st);
 
