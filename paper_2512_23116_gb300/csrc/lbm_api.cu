@@ -104,7 +104,6 @@ struct lbm_s {
   std::map<GraphKey, cudaGraphExec_t> graphs;
   bool use_graphs = true;
   long long wait_ns = 2000000000ll;  // bound of device-side waits
-  int pdl = 1;                       // steps of the TMA kernel with programmatic dependent launch
   int inject_withhold = 0;           // test hook, consumed by the next TMA step launch
   long long inject_wait_ns = 0;
   std::string err;
@@ -360,18 +359,12 @@ cudaError_t launch_step(lbm_t h, const LaunchArgs& la) {
 
 // Enqueue steps t0 .. t0 + n - 1 (no host state change).
 int enqueue_steps(lbm_t h, int64_t t0, int64_t n) {
-  bool prev_plain = false;  // the previous operation in the stream is a plain step kernel
   for (int64_t k = 0; k < n; ++k) {
     const int64_t t = t0 + k;
     const bool stats = h->stats_every > 0 && (t % h->stats_every) == 0;
     LaunchArgs la = base_args(h);
     la.odd = (t & 1) != 0;
     la.mode = stats ? MODE_STEP_STATS : MODE_STEP;
-    // programmatic dependent launch only from one plain step to the next: a
-    // statistics step follows a memset of its partials and is followed by the
-    // finisher, which must see it whole
-    la.pdl = h->pdl && prev_plain && !stats;
-    prev_plain = !stats;
     if (stats)
       CK(h, cudaMemsetAsync(h->d_partials, 0, h->partials_elems * sizeof(double), h->stream));
     CK(h, launch_step(h, la));

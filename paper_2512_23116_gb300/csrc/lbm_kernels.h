@@ -27,25 +27,6 @@ inline cudaError_t launch_kernel(void (*kernel)(P...), dim3 grid, dim3 block, si
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
 }
 
-// The same with programmatic dependent launch allowed: the kernel may be
-// scheduled while the previous kernel in the stream is finishing, and must
-// execute griddepcontrol.wait before it touches that kernel's results.
-template <typename... P, typename... A>
-inline cudaError_t launch_kernel_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-                                     A&&... args) {
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cudaLaunchConfig_t cfg{};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
-}
-
 struct LaunchArgs {
   const InstDesc* insts;   // device table
   int ninst;
@@ -67,7 +48,6 @@ struct LaunchArgs {
   int withhold_first_load; // test hook: block 0 never loads its first tile
   int hist_smem;           // TMA statistics pass: byte offset of the theta histogram in
                            // dynamic shared memory (0: global counts)
-  int pdl;                 // launch with programmatic dependent launch (step kernels)
 };
 
 cudaError_t launch_step_direct(const LaunchArgs& la, cudaStream_t st);

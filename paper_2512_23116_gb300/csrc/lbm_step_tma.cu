@@ -613,13 +613,6 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
     fence_async_smem();
   }
   __syncthreads();
-  // Programmatic dependent launch (the steps are launched with it): the next
-  // step's grid may be scheduled once every block of this one has started, and
-  // this grid waits for the previous step's grid to complete, its stores
-  // visible, before anything below reads the populations.  Launched without
-  // the attribute, both instructions do nothing.
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  asm volatile("griddepcontrol.wait;" ::: "memory");
 
   if (warp == nconsumer_warps) {
     // ---------------- producer warp: lane j < 19 issues segment j's bulk copies (lane g < 9
@@ -815,10 +808,6 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
 
 template <typename T, bool ODD, int MODE, int SLOT>
 cudaError_t launch_tma_t(const LaunchArgs& la, cudaStream_t st) {
-  if (la.pdl)
-    return launch_kernel_pdl(k_step_tma<T, ODD, MODE, SLOT>, la.grid, la.threads, la.smem_bytes, st, la.insts,
-                             la.ninst, la.tile_lo, la.tile_hi, la.sa, la.stages, la.tile_bytes_max, la.err,
-                             la.wait_ns, la.withhold_first_load, la.dout, la.hist_smem);
   return launch_kernel(k_step_tma<T, ODD, MODE, SLOT>, la.grid, la.threads, la.smem_bytes, st, la.insts,
                        la.ninst, la.tile_lo, la.tile_hi, la.sa, la.stages, la.tile_bytes_max, la.err,
                        la.wait_ns, la.withhold_first_load, la.dout, la.hist_smem);
