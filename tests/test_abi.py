@@ -83,6 +83,9 @@ int main(void) {
     (dict(nx=8, nu0=0.01, force_mode=9), "force_mode"),
     (dict(nx=8, nu0=0.01, hist_bins=-1), "hist_bins"),
     (dict(nx=8, nu0=0.01, kernel=5), "kernel"),
+    (dict(nx=8, nu0=0.01, tma_slots=3), "tma_slots"),
+    (dict(nx=8, nu0=0.01, layout=3), "layout"),
+    (dict(nx=8, nu0=0.01, strain_mode=2), "strain_mode"),
 ])
 def test_invalid_parameters_rejected_before_any_device_call(lib, kw, frag):
     nx = kw.pop("nx")

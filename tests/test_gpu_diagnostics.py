@@ -244,6 +244,11 @@ def test_invalid_calls_on_a_live_handle(gpu_lib):
             assert ei.value.code == lbm.LBM_ERR_INVALID_ARG
         gpu.step(1)
         gpu.sync()
+    # the two-block slot layout needs two stages whose tile rows fit its slots
+    p = lbm.make_params(64, nu0=0.01, kernel=2, tile_rows=2, stages=3, threads=256, tma_slots=2)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_create(p)
+    assert ei.value.code == lbm.LBM_ERR_UNSUPPORTED and "tma_slots" in str(ei.value)
 
 
 def test_energy_balance_series_matches_oracle(gpu_lib):
