@@ -52,24 +52,39 @@ def run_with_statistics(lattice, steps: int, every: int, path: str, inst: int = 
     stem = os.path.splitext(path)[0]
     records = []
     done = 0
+    if steps > 0:
+        n = min(every, steps)
+        lbm_step(lattice.h, n)
+        done = n
     with open(path, "a") as fh:
-        while done < steps:
-            n = min(every, steps - done)
-            lbm_step(lattice.h, n)
-            done += n
+        while records or done > 0:
+            # statistics of the state after `done` steps (these calls wait for
+            # the steps enqueued before them)
             st = lbm_stats(lattice.h, inst, what)
-            rec = {k: _plain(v) for k, v in st.items()}
-            if spectrum:
-                rec["E"] = _plain(lbm_spectrum(lattice.h, inst, kmax))
+            E = lbm_spectrum(lattice.h, inst, kmax) if spectrum else None
+            sl = None
             if theta_slice is not None:
-                axis, index = theta_slice
-                sl = lbm_get_theta_slice(lattice.h, inst, axis, index, lattice.shapes[inst])
+                sl = lbm_get_theta_slice(lattice.h, inst, theta_slice[0], theta_slice[1], lattice.shapes[inst])
+            # enqueue the next interval, so that the device steps while the
+            # host writes this record
+            more = done < steps
+            if more:
+                n = min(every, steps - done)
+                lbm_step(lattice.h, n)
+                done += n
+            rec = {k: _plain(v) for k, v in st.items()}
+            if E is not None:
+                rec["E"] = _plain(E)
+            if sl is not None:
                 fname = f"{stem}_theta_t{st['step']}.npy"
                 np.save(fname, sl)
-                rec["theta_slice"] = {"axis": axis, "index": index, "file": os.path.basename(fname)}
+                rec["theta_slice"] = {"axis": theta_slice[0], "index": theta_slice[1],
+                                      "file": os.path.basename(fname)}
             fh.write(json.dumps(rec) + "\n")
             fh.flush()
             records.append(rec)
+            if not more:
+                break
     return records
 
 
