@@ -743,7 +743,9 @@ def main():
                 "algorithmic_bytes_per_launch": cells * BYTES_PER_UPDATE[0]}
 
     extra = {}
-    if not args.no_extra:
+    # the extra workloads and studies run in single-GPU runs only (a replicas
+    # run measures the headline workload on every rank)
+    if not args.no_extra and not dist:
         def guarded(name, fn):
             # one failing study is recorded in the line, not fatal to it
             try:
