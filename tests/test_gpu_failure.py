@@ -54,3 +54,21 @@ def test_debug_hook_arguments(gpu_lib):
             with pytest.raises(lbm.LbmError) as ei:
                 lbm.lbm_debug_withhold_load(L.h, bad)
             assert ei.value.code == lbm.LBM_ERR_INVALID_ARG
+
+
+def test_allocation_failure_is_reported_not_raised(gpu_lib):
+    """A lattice larger than the device (8192 x 8192 x 128 cells need 653 GB of
+    FP32 populations) fails to allocate: lbm_create returns LBM_ERR_OOM with
+    the size in the text, releases what it had allocated, and the next handle
+    works (a real allocation failure, no test hook needed)."""
+    lbm = gpu_lib
+    p = lbm.make_params(8192, 8192, 128, nu0=0.01)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_create(p)
+    assert ei.value.code == lbm.LBM_ERR_OOM
+    assert "population array" in str(ei.value)
+    with lbm.Lattice(lbm.make_params(16, nu0=0.01)) as L:
+        L.init(lbm.LBM_INIT_TGV3D, amplitude=0.05)
+        L.step(4)
+        L.sync()
+        assert np.isfinite(L.populations()).all()
