@@ -65,12 +65,7 @@ struct Inst {
 
 struct GraphKey {
   int64_t phase, len;
-  int grp;  // instance group of a batched handle (0: every instance)
-  bool operator<(const GraphKey& o) const {
-    if (phase != o.phase) return phase < o.phase;
-    if (len != o.len) return len < o.len;
-    return grp < o.grp;
-  }
+  bool operator<(const GraphKey& o) const { return phase != o.phase ? phase < o.phase : len < o.len; }
 };
 
 }  // namespace
@@ -107,14 +102,6 @@ struct lbm_s {
   double* d_spec = nullptr;
   size_t spec_elems = 0;
   std::map<GraphKey, cudaGraphExec_t> graphs;
-  // Batched handles whose instances outgrow the L2: consecutive instances
-  // grouped into tile ranges of at most l2_budget bytes of populations (an
-  // instance larger than that joins its larger neighbours in one group); a
-  // run of steps without a statistics step advances one group after the other
-  // through the whole run, so each group's populations stay in L2 between
-  // its steps.  Empty: every step covers every instance.
-  std::vector<std::pair<int64_t, int64_t>> groups;
-  int64_t l2_budget = 0;
   bool use_graphs = true;
   long long wait_ns = 2000000000ll;  // bound of device-side waits
   int inject_withhold = 0;           // test hook, consumed by the next TMA step launch
@@ -321,30 +308,6 @@ int build_tiles(lbm_t h) {
     d.f_elems = (int64_t)(I.f_bytes / h->esize);
   }
   h->total_tiles = tile;
-  // instance groups of a batched handle whose populations outgrow the L2
-  h->groups.clear();
-  int64_t all_bytes = 0;
-  for (const Inst& I : h->inst) all_bytes += (int64_t)I.f_bytes;
-  if (h->inst.size() > 1 && h->l2_budget > 0 && all_bytes > h->l2_budget) {
-    size_t i = 0;
-    while (i < h->inst.size()) {
-      size_t j = i;
-      int64_t bytes = 0;
-      const bool big = (int64_t)h->inst[i].f_bytes > h->l2_budget;
-      // small instances fill a group up to the budget; instances larger than
-      // the budget run together (they stream from HBM in any case)
-      while (j < h->inst.size()) {
-        const int64_t b = (int64_t)h->inst[j].f_bytes;
-        if (big ? b <= h->l2_budget : (bytes + b > h->l2_budget && j > i)) break;
-        bytes += b;
-        ++j;
-        if (!big && bytes >= h->l2_budget) break;
-      }
-      h->groups.emplace_back(h->inst[i].tile_begin, h->inst[j - 1].tile_end);
-      i = j;
-    }
-    if (h->groups.size() < 2) h->groups.clear();
-  }
   CK(h, cudaMemcpyAsync(h->d_desc, h->h_desc.data(), sizeof(InstDesc) * h->h_desc.size(),
                         cudaMemcpyHostToDevice, h->stream));
   // partials for every block and instance
@@ -395,13 +358,11 @@ cudaError_t launch_step(lbm_t h, const LaunchArgs& la) {
 }
 
 // Enqueue steps t0 .. t0 + n - 1 (no host state change).
-int enqueue_steps(lbm_t h, int64_t t0, int64_t n, int64_t tile_lo = 0, int64_t tile_hi = -1) {
+int enqueue_steps(lbm_t h, int64_t t0, int64_t n) {
   for (int64_t k = 0; k < n; ++k) {
     const int64_t t = t0 + k;
     const bool stats = h->stats_every > 0 && (t % h->stats_every) == 0;
     LaunchArgs la = base_args(h);
-    la.tile_lo = tile_lo;
-    la.tile_hi = tile_hi < 0 ? h->total_tiles : tile_hi;
     la.odd = (t & 1) != 0;
     la.mode = stats ? MODE_STEP_STATS : MODE_STEP;
     if (stats)
@@ -425,36 +386,6 @@ int64_t schedule_period(lbm_t h) {
   return 2 / a * h->stats_every;  // lcm(2, stats_every)
 }
 
-// Steps t0 .. t0 + len - 1 over tiles [lo, hi) (hi < 0: every tile), replayed
-// from a graph captured once per (schedule phase, len, group) when len is a
-// whole chunk.
-int run_chunk(lbm_t h, int64_t t0, int64_t len, int grp, int64_t lo, int64_t hi, bool graph) {
-  if (!graph) return enqueue_steps(h, t0, len, lo, hi);
-  GraphKey key{t0 % schedule_period(h), len, grp};
-  auto it = h->graphs.find(key);
-  if (it == h->graphs.end()) {
-    cudaGraph_t g = nullptr;
-    const bool pending = cudaPeekAtLastError() != cudaSuccess;  // the caller's, left alone
-    CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    const int rc = enqueue_steps(h, t0, len, lo, hi);
-    cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
-    if (rc != LBM_OK) {
-      if (g) cudaGraphDestroy(g);
-      // the invalidated capture's own error; the cause is in h->err
-      if (!pending) (void)cudaGetLastError();
-      return rc;
-    }
-    CK(h, ce);
-    cudaGraphExec_t ex = nullptr;
-    cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
-    cudaGraphDestroy(g);
-    CK(h, ie);
-    it = h->graphs.emplace(key, ex).first;
-  }
-  CK(h, cudaGraphLaunch(it->second, h->stream));
-  return LBM_OK;
-}
-
 int run_steps(lbm_t h, int64_t n) {
   if (n > 0) ++h->version;
   int64_t done = 0;
@@ -462,18 +393,32 @@ int run_steps(lbm_t h, int64_t n) {
   while (done < n) {
     const int64_t len = std::min(chunk, n - done);
     const int64_t t0 = h->t;
-    bool stats_in_chunk = false;
-    for (int64_t k = 0; k < len && h->stats_every > 0; ++k)
-      stats_in_chunk = stats_in_chunk || (t0 + k) % h->stats_every == 0;
-    const bool graph = h->use_graphs && len == chunk;
-    if (!h->groups.empty() && !stats_in_chunk) {
-      // instance groups one after the other, each through the whole chunk
-      for (size_t gi = 0; gi < h->groups.size(); ++gi) {
-        const int rc = run_chunk(h, t0, len, (int)gi + 1, h->groups[gi].first, h->groups[gi].second, graph);
-        if (rc != LBM_OK) return rc;
+    int rc;
+    if (h->use_graphs && len == chunk) {
+      GraphKey key{t0 % schedule_period(h), len};
+      auto it = h->graphs.find(key);
+      if (it == h->graphs.end()) {
+        cudaGraph_t g = nullptr;
+        const bool pending = cudaPeekAtLastError() != cudaSuccess;  // the caller's, left alone
+        CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        rc = enqueue_steps(h, t0, len);
+        cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
+        if (rc != LBM_OK) {
+          if (g) cudaGraphDestroy(g);
+          // the invalidated capture's own error; the cause is in h->err
+          if (!pending) (void)cudaGetLastError();
+          return rc;
+        }
+        CK(h, ce);
+        cudaGraphExec_t ex = nullptr;
+        cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        CK(h, ie);
+        it = h->graphs.emplace(key, ex).first;
       }
+      CK(h, cudaGraphLaunch(it->second, h->stream));
     } else {
-      const int rc = run_chunk(h, t0, len, 0, 0, -1, graph);
+      rc = enqueue_steps(h, t0, len);
       if (rc != LBM_OK) return rc;
     }
     for (int64_t k = 0; k < len; ++k) {
@@ -741,11 +686,6 @@ int create_impl(const lbm_params* params, int count, lbm_t* out) {
   h->esize = h->precision == LBM_FP32 ? 4 : 2;
   h->stats_every = params[0].stats_every;
   cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
-  {
-    int l2 = 0;
-    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->device);
-    h->l2_budget = (int64_t)l2 * 5 / 8;  // room for the other groups' write-backs in flight
-  }
   if (params[0].stream) {
     h->stream = static_cast<cudaStream_t>(params[0].stream);
   } else {

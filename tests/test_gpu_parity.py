@@ -497,28 +497,3 @@ def test_shear_wave_advected_by_a_uniform_flow(gpu_lib, kind):
     assert np.isclose(np.log(abs(c1) / abs(c0)), -nu0 * k * k * T, rtol=1e-2)
     dphi = np.angle(c1 / c0) + k * U * T
     assert abs((dphi + np.pi) % (2 * np.pi) - np.pi) <= 1e-3
-
-
-def test_batch_in_l2_sized_groups_is_bitwise_the_whole_batch(gpu_lib):
-    """A batch whose populations outgrow the L2 advances runs of steps without
-    a statistics step one instance group at a time (three 64^3 instances per
-    group, the two 128^3 instances together); with a statistics step in every
-    run of steps the same batch advances every instance in each launch.  Both
-    schedules give bitwise-equal populations, through graph-replayed chunks
-    and a ragged tail."""
-    lbm = gpu_lib
-    sizes = [64, 64, 64, 64, 128, 128]
-    cfg = dict(kernel=2, tile_rows=2, stages=2, threads=256)
-    us = [synthetic.random_solenoidal(n, seed=20 + i, urms=0.03) for i, n in enumerate(sizes)]
-    out = []
-    for every in (0, 1):
-        params = [lbm.make_params(n, nu0=0.002, cs=0.13, f0=1e-5, force_mode=lbm.LBM_FORCE_PAPER_SIN,
-                                  stats_every=every, **cfg) for n in sizes]
-        with lbm.Lattice(params) as L:
-            for i, u in enumerate(us):
-                L.init(lbm.LBM_INIT_VELOCITY, u=u, inst=i)
-            L.step(70)
-            L.sync()
-            out.append([L.populations(inst=i) for i in range(len(sizes))])
-    for a, b in zip(out[0], out[1]):
-        assert np.array_equal(a, b)
