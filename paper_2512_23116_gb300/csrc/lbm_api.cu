@@ -631,9 +631,9 @@ int alloc_common(lbm_t h) {
   CK(h, cudaMalloc(&h->d_desc, sizeof(InstDesc) * h->inst.size()));
   CK(h, cudaMalloc(&h->d_results, sizeof(double) * kNP * h->inst.size()));
   CK(h, cudaMalloc(&h->d_ring, sizeof(double) * kNP * h->inst.size() * kRingCap));
-  CK(h, cudaMalloc(&h->d_seq, sizeof(unsigned long long)));
+  CK(h, cudaMalloc(&h->d_seq, 2 * sizeof(unsigned long long)));
   CK(h, cudaMalloc(&h->d_err, sizeof(uint32_t)));
-  CK(h, cudaMemsetAsync(h->d_seq, 0, sizeof(unsigned long long), h->stream));
+  CK(h, cudaMemsetAsync(h->d_seq, 0, 2 * sizeof(unsigned long long), h->stream));
   CK(h, cudaMemsetAsync(h->d_err, 0, sizeof(uint32_t), h->stream));
   return LBM_OK;
 }
@@ -994,7 +994,7 @@ int reset_time(lbm_t h) {
     h->t = 0;
     h->rec_steps.clear();
     h->inst[0].rec_read = 0;
-    CK(h, cudaMemsetAsync(h->d_seq, 0, sizeof(unsigned long long), h->stream));
+    CK(h, cudaMemsetAsync(h->d_seq, 0, 2 * sizeof(unsigned long long), h->stream));
   }
   return LBM_OK;
 }

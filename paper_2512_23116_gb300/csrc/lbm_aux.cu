@@ -3,6 +3,7 @@
 // of the energy spectrum and the structure-function reductions.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cfloat>
 
 #include "lbm_device.cuh"
@@ -145,27 +146,47 @@ __global__ void k_relayout(InstDesc d, bool from_odd, int a, const T* __restrict
   }
 }
 
+// One warp per output value: lane l folds blocks l, l + 32, ... in that order,
+// then a fixed shuffle tree combines the lanes, so a result depends only on
+// the partials and the grid size, never on scheduling.  seq[0] counts the
+// records in the ring; seq[1] counts the blocks of a launch that are done, and
+// the last of them advances seq[0] (every block has read it by then).
 __global__ void k_finish(const double* __restrict__ partials, int ninst, int grid,
                          double* __restrict__ results, double* ring, unsigned long long* seq,
                          int cap, uint32_t* err) {
-  const unsigned long long slot = ring ? (*seq % (unsigned long long)cap) : 0ull;
-  for (int idx = threadIdx.x; idx < ninst * kNP; idx += blockDim.x) {
+  const unsigned long long slot = ring ? (__ldcg(seq) % (unsigned long long)cap) : 0ull;
+  const int lane = threadIdx.x & 31;
+  const int warps = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int idx = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); idx < ninst * kNP; idx += warps) {
     const int i = idx / kNP, k = idx - i * kNP;
-    double r = (k == P_THMIN) ? DBL_MAX : (k == P_THMAX ? -DBL_MAX : 0.0);
-    for (int b = 0; b < grid; ++b) {
+    const bool lo = k == P_THMIN, hi = k == P_THMAX;
+    double r = lo ? DBL_MAX : (hi ? -DBL_MAX : 0.0);
+    for (int b = lane; b < grid; b += 32) {
       const double* p = partials + ((int64_t)i * grid + b) * kNP;
       if (p[P_CELLS] == 0.0) continue;  // block saw no cell of instance i
       const double v = p[k];
-      if (k == P_THMIN) r = fmin(r, v);
-      else if (k == P_THMAX) r = fmax(r, v);
-      else r += v;
+      r = lo ? fmin(r, v) : (hi ? fmax(r, v) : r + v);
     }
-    results[idx] = r;
-    if (k == P_BAD && r > 0.0) atomicOr(err, ERR_NONFINITE);
-    if (ring) ring[slot * (unsigned long long)(ninst * kNP) + idx] = r;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const double o = __shfl_down_sync(0xffffffffu, r, off);
+      r = lo ? fmin(r, o) : (hi ? fmax(r, o) : r + o);
+    }
+    if (lane == 0) {
+      results[idx] = r;
+      if (k == P_BAD && r > 0.0) atomicOr(err, ERR_NONFINITE);
+      if (ring) ring[slot * (unsigned long long)(ninst * kNP) + idx] = r;
+    }
   }
+  if (!ring) return;
   __syncthreads();
-  if (ring && threadIdx.x == 0) *seq += 1ull;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(seq + 1, 1ull) == (unsigned long long)gridDim.x - 1ull) {
+      seq[0] += 1ull;
+      seq[1] = 0ull;
+    }
+  }
 }
 
 // Exact integer shell: s with s^2 - s + 1 <= K <= s^2 + s (s - 1/2 <= sqrt K < s + 1/2).
@@ -207,11 +228,17 @@ __global__ void k_spec_bin(const float2* __restrict__ c, int nx, int ny, int nz,
     partials[(int64_t)blockIdx.x * (kmax + 1) + s] += sh[s];
 }
 
+// Column sums of a [rows][cols] table, one warp per column in the fixed order
+// of k_finish (lane l adds rows l, l + 32, ...; then a shuffle tree).
 __global__ void k_sum_cols(const double* __restrict__ p, int rows, int cols, double* __restrict__ out) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int c = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); c < cols; c += warps) {
     double r = 0.0;
-    for (int b = 0; b < rows; ++b) r += p[(int64_t)b * cols + c];
-    out[c] = r;
+    for (int b = lane; b < rows; b += 32) r += p[(int64_t)b * cols + c];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) r += __shfl_down_sync(0xffffffffu, r, off);
+    if (lane == 0) out[c] = r;
   }
 }
 
@@ -417,7 +444,9 @@ cudaError_t launch_relayout_pair(const InstDesc& d, int precision, bool from_odd
 cudaError_t launch_finish(const double* partials, int ninst, int grid, double* results,
                           double* ring, unsigned long long* seq, int cap, uint32_t* err,
                           cudaStream_t st) {
-  return launch_kernel(k_finish, 1, 256, 0, st, partials, ninst, grid, results, ring, seq, cap, err);
+  const int warps_per_block = 256 / 32;
+  const int blocks = std::max(1, std::min(1024, (ninst * kNP + warps_per_block - 1) / warps_per_block));
+  return launch_kernel(k_finish, blocks, 256, 0, st, partials, ninst, grid, results, ring, seq, cap, err);
 }
 
 cudaError_t launch_spec_bin(const void* coeffs, int nx, int ny, int nz, int kmax,
@@ -433,7 +462,8 @@ cudaError_t launch_spec_finish(const double* partials, int blocks, int kmax, dou
 
 cudaError_t launch_sum_cols(const double* partials, int rows, int cols, double* out,
                             cudaStream_t st) {
-  return launch_kernel(k_sum_cols, (cols + 255) / 256, 256, 0, st, partials, rows, cols, out);
+  const int blocks = std::max(1, std::min(1024, (cols + 7) / 8));  // 8 warps per block, a warp per column
+  return launch_kernel(k_sum_cols, blocks, 256, 0, st, partials, rows, cols, out);
 }
 
 cudaError_t launch_struct_multi(const float* u, int nx, int ny, int nz, const int* r, int nr, double* partials,

@@ -99,7 +99,9 @@ cudaError_t launch_set_pop(const InstDesc& d, int precision, bool odd, int a, co
 cudaError_t launch_relayout_pair(const InstDesc& d, int precision, bool from_odd, int a,
                                  void* scratch, cudaStream_t st);
 // Reduce block partials: results[i][kNP] for instances i in [0, ninst); when
-// ring != null also append to ring[(seq % cap)][ninst][kNP] and bump *seq.
+// ring != null also append to ring[(seq[0] % cap)][ninst][kNP] and bump seq[0]
+// (seq points at two words: the record count and a block counter kept at 0
+// between launches).
 cudaError_t launch_finish(const double* partials, int ninst, int grid, double* results,
                           double* ring, unsigned long long* seq, int cap, uint32_t* err,
                           cudaStream_t st);

@@ -300,3 +300,34 @@ def test_batch_entry_points_and_velocity(gpu_lib):
             assert np.abs(u).max() > 0.01
     finally:
         lbm.lbm_destroy(h)
+
+
+def test_series_many_instances_match_single_handles(gpu_lib):
+    """In-step records of a 16-instance handle (320 reduced values, so the
+    reduction spans many blocks, replayed from captured graphs): one record per
+    statistics step for every instance, each equal to the record of the same
+    instance advanced in a handle of its own."""
+    lbm = gpu_lib
+    shapes = [(8 + (i % 4) * 2, 6 + (i % 3) * 4, 10 + (i % 5)) for i in range(16)]
+    params = [lbm.make_params(nx, ny, nz, nu0=0.01 + 0.001 * i, cs=0.13 if i % 2 else 0.0, stats_every=3)
+              for i, (nz, ny, nx) in enumerate(shapes)]
+    amps = [0.01 + 0.002 * i for i in range(16)]
+    steps = 70
+    with lbm.Lattice(params) as g:
+        for i, a in enumerate(amps):
+            g.init(lbm.LBM_INIT_TGV3D, amplitude=a, inst=i)
+        g.step(steps)
+        batch = [g.series(inst=i) for i in range(16)]
+    want_steps = list(range(0, steps, 3))
+    for i in (0, 5, 10, 15):
+        with lbm.Lattice(params[i]) as one:
+            one.init(lbm.LBM_INIT_TGV3D, amplitude=amps[i])
+            one.step(steps)
+            single = one.series()
+        assert [r["step"] for r in single] == want_steps
+        for rb, rs in zip(batch[i], single):
+            for k in ("E_k", "eps0", "theta_mean", "theta_max", "theta_min"):
+                assert math.isclose(rb[k], rs[k], rel_tol=1e-6, abs_tol=1e-30), (i, rb["step"], k)
+    for i in range(16):
+        assert [r["step"] for r in batch[i]] == want_steps, i
+        assert math.isclose(batch[i][0]["E_k"], amps[i] ** 2 / 8, rel_tol=1e-5), i
