@@ -516,7 +516,7 @@ def c_sweep(lbm, device, stream, n=128, re=5000.0, cs=(0.0, 0.1, 0.16, 0.25), st
     return {"n": n, "Re": re, "steps": steps, "c_sweep": out}
 
 
-def les_c2_run(lbm, device, stream, n=100, steps=20000, every=500, plane=50):
+def les_c2_run(lbm, device, stream, n=100, steps=20000, every=500, plane=50, spread_seeds=(2, 3)):
     """The paper's LES workload as one job (Sec. 3.1, Sec. 4.1): n^3, C = 0.13,
     nu0 from Re = 2e4, the paper's forcing, from the seeded random field,
     `steps` steps with the statistics cadence of the paper's post-processing
@@ -532,7 +532,8 @@ def les_c2_run(lbm, device, stream, n=100, steps=20000, every=500, plane=50):
     (Sec. 4.1: mean ~1.34e-3, 5th percentile > 1.0e-3, 95th <~ 1.82e-3, maxima
     up to ~3.7e-3), context only: the paper's statistics are over t/t0 in
     [200, 600] of a stationary state, this run starts from the synthetic
-    field."""
+    field.  The same job from the seeds `spread_seeds` (untimed) gives the
+    seed-to-seed spread of those late-time statistics."""
     import tempfile
 
     import torch
@@ -561,13 +562,26 @@ def les_c2_run(lbm, device, stream, n=100, steps=20000, every=500, plane=50):
             fused = L.series()
             wall_cadence = time.perf_counter() - t0
         lines = len(series.read_series(path))
-        late = []
-        for r in recs:
-            if r["step"] >= steps // 2:
-                sl = np.load(os.path.join(tmp, r["theta_slice"]["file"]))
-                late.append((r["theta_mean"], r["theta_p05"], r["theta_p50"], r["theta_p95"], r["theta_p99"],
-                             r["theta_max"], float(sl.mean()), float(sl.max()), r["F4"][0], r["Re_lambda"],
-                             r["E_k"]))
+
+        def late_rows(records):
+            rows = []
+            for r in records:
+                if r["step"] >= steps // 2:
+                    sl = np.load(os.path.join(tmp, r["theta_slice"]["file"]))
+                    rows.append((r["theta_mean"], r["theta_p05"], r["theta_p50"], r["theta_p95"],
+                                 r["theta_p99"], r["theta_max"], float(sl.mean()), float(sl.max()), r["F4"][0],
+                                 r["Re_lambda"], r["E_k"]))
+            return np.array(rows)
+
+        late = late_rows(recs)
+        per_seed = [late.mean(axis=0)]
+        for seed in spread_seeds:
+            with lbm.Lattice(params(every)) as L:
+                L.init_random(seed=seed, urms=URMS, k0=K0)
+                sp = os.path.join(tmp, f"c2_series_seed{seed}.jsonl")
+                per_seed.append(late_rows(series.run_with_statistics(L, steps, every, sp,
+                                                                     theta_slice=(2, plane))).mean(axis=0))
+        per_seed = np.array(per_seed)
     with lbm.Lattice(params(0)) as L:
         L.init_random(seed=SEED, urms=URMS, k0=K0)
         L.sync()
@@ -578,9 +592,10 @@ def les_c2_run(lbm, device, stream, n=100, steps=20000, every=500, plane=50):
         wall_plain = time.perf_counter() - t0
         cfg = L.config()
     last = recs[-1]
-    a = np.array(late)
+    a = late
     names = ("theta_mean", "theta_p05", "theta_p50", "theta_p95", "theta_p99", "theta_max",
              "slice_theta_mean", "slice_theta_max", "F4_r1", "Re_lambda", "E_k")
+    seeds = (SEED,) + tuple(spread_seeds)
     return {"n": n, "steps": steps, "every": every, "C": 0.13, "nu0": nu0, "theta_molecular_3nu0": 3 * nu0,
             "records": len(recs), "jsonl_lines": lines, "fused_records": len(fused),
             "wall_s_with_statistics_cadence": wall_cadence, "wall_s_steps_only": wall_plain,
@@ -591,6 +606,11 @@ def les_c2_run(lbm, device, stream, n=100, steps=20000, every=500, plane=50):
             "statistics_overhead_with_first_call": (wall_cadence + first_call) / wall_plain - 1.0,
             "late_time_mean": {k: float(v) for k, v in zip(names, a.mean(axis=0))},
             "late_time_max_theta": float(a[:, 5].max()),
+            "seed_spread": {"seeds": list(seeds),
+                            "late_time_mean_by_seed": {k: [float(v) for v in per_seed[:, j]]
+                                                       for j, k in enumerate(names)},
+                            "relative_std": {k: float(per_seed[:, j].std(ddof=1) / abs(per_seed[:, j].mean()))
+                                             for j, k in enumerate(names) if len(seeds) > 1}},
             "paper_context_sec_4_1": {"theta_mean": 1.34e-3, "theta_p05_above": 1.0e-3,
                                       "theta_p95_below": 1.82e-3, "theta_max_up_to": 3.68e-3},
             "final": {"E_k": last["E_k"], "Re_lambda": last["Re_lambda"], "eta": last["eta"], "L": last["L"],
