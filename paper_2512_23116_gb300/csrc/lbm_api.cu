@@ -30,6 +30,7 @@ namespace {
 using namespace lbm;
 
 constexpr int kRingCap = 1024;
+constexpr int kMinHistWindow = 256;  // fewer histogram bins than this in shared memory: all global
 constexpr int64_t kChunkCells = 4 << 20;
 constexpr double kPi = 3.14159265358979323846;
 
@@ -488,10 +489,18 @@ int diag_pass(lbm_t h, int i, bool want_u, bool want_aux, int plane_axis, int pl
   int grid = 0;
   if (h->kind == 2) {
     LaunchArgs lt = la;
-    const int hist_bytes = (I.hist_bins + 1) * 4;
-    const int smem_hist = (h->smem + hist_bytes + 15) / 16 * 16;
-    if (want_hist && smem_hist <= kMaxDynSmem && tma_prepare(h->precision, smem_hist) == cudaSuccess) {
+    // as many histogram bins as fit behind the stages, from the bin of theta
+    // = 3 nu0 up (theta = 3 nu0 + 3 C |S| is never below it; one bin of
+    // margin for rounding, and a cell outside the window is still counted,
+    // in global memory)
+    const double b3 = 3.0 * I.nu0 * I.hist_bins / I.hist_max;  // bin of theta = 3 nu0
+    const int lo = b3 >= (double)I.hist_bins ? I.hist_bins : std::max(0, (int)b3 - 1);
+    const int win = std::min(I.hist_bins + 1 - lo, (tma_diag_smem_limit(h->precision) - h->smem) / 4);
+    const int smem_hist = (h->smem + 4 * win + 15) / 16 * 16;
+    if (want_hist && win >= kMinHistWindow && tma_prepare(h->precision, smem_hist) == cudaSuccess) {
       lt.hist_smem = h->smem;
+      lt.hist_lo = lo;
+      lt.hist_win = win;
       lt.smem_bytes = smem_hist;
     }
     // the pass is bound by its consumers' arithmetic, not by the copies: as

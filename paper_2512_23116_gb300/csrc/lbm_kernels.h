@@ -48,6 +48,8 @@ struct LaunchArgs {
   int withhold_first_load; // test hook: block 0 never loads its first tile
   int hist_smem;           // TMA statistics pass: byte offset of the theta histogram in
                            // dynamic shared memory (0: global counts)
+  int hist_lo, hist_win;   // bins [hist_lo, hist_lo + hist_win) of it counted in shared memory
+                           // (hist_smem > 0), the rest in the global counts
 };
 
 cudaError_t launch_step_direct(const LaunchArgs& la, cudaStream_t st);
@@ -77,6 +79,9 @@ int tma_smem_bytes(int stages, int tile_bytes, int max_nx);
 // read-only statistics pass (diag = true).
 int tma_max_blocks_per_sm(int precision, int slot_bytes, int threads, int smem_bytes, bool diag = false);
 cudaError_t tma_prepare(int precision, int smem_bytes);
+// Largest dynamic shared memory a launch of the read-only statistics pass can
+// take (0 when the query fails).
+int tma_diag_smem_limit(int precision);
 
 // Initial condition: f' = equilibrium of (drho, u), written at AA parity `odd`,
 // for the canonical cells [c0, c0 + n) (linear index (z ny + y) nx + x).

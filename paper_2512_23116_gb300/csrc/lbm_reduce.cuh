@@ -94,34 +94,36 @@ struct Acc {
 // A thread's run of cells in one theta-histogram bin: the count goes to the
 // histogram (one atomic add) when the bin changes and at the end.  Theta
 // concentrates in a few bins, so per-cell increments, even warp-aggregated
-// ones, would serialise on the same words.  Counts in global memory (a
-// histogram too large for the block's shared memory) are also summed over the
-// warp's lanes that flush the same bin: contended atomics in L2 cost far more
-// than the match; in shared memory they do not.
+// ones, would serialise on the same words.  Bins [lo, lo + win) are counted in
+// shared memory `sm` (at bin - lo); the others (when `gl` is not null) in the
+// global counts `gl`, summed first over the warp's lanes that flush the same
+// bin: contended atomics in L2 cost far more than the match; in shared memory
+// they do not.
 struct HistRun {
   int bin = -1;
   uint32_t n = 0;
 
-  // Called by every active lane; lanes with `go` add their run.
-  __device__ __forceinline__ void flush_if(uint32_t* hist, bool go, bool global) {
+  // Called by every active lane; lanes with `go` add their run.  gl is null
+  // (for the whole block) when the window holds every bin.
+  __device__ __forceinline__ void flush_if(uint32_t* sm, int lo, int win, uint32_t* gl, bool go) {
     go = go && n > 0;
-    if (!global) {
-      if (go) {
-        atomicAdd(&hist[bin], n);
-        n = 0;
+    const bool local = go && (unsigned)(bin - lo) < (unsigned)win;
+    if (local) atomicAdd(&sm[bin - lo], n);
+    if (gl) {
+      const bool far = go && !local;
+      const unsigned fl = __ballot_sync(__activemask(), far);
+      if (far) {
+        const unsigned grp = __match_any_sync(fl, bin);
+        const unsigned tot = __reduce_add_sync(grp, n);
+        if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&gl[bin], tot);
       }
-      return;
     }
-    const unsigned fl = __ballot_sync(__activemask(), go);
-    if (go) {
-      const unsigned grp = __match_any_sync(fl, bin);
-      const unsigned tot = __reduce_add_sync(grp, n);
-      if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&hist[bin], tot);
-      n = 0;
-    }
+    if (go) n = 0;
   }
 
-  __device__ __forceinline__ void flush(uint32_t* hist, bool global) { flush_if(hist, true, global); }
+  __device__ __forceinline__ void flush(uint32_t* sm, int lo, int win, uint32_t* gl) {
+    flush_if(sm, lo, win, gl, true);
+  }
 };
 
 // Reduce the accumulators of the `nthreads` threads that call this (a whole
@@ -176,12 +178,13 @@ static __device__ __forceinline__ void block_flush(Acc& acc, double* __restrict_
   named_sync(bar_id, nthreads);
 }
 
-// Per-cell outputs of the read-only diagnostic pass; `hist` (shared-memory
-// counts, or global ones when hist_global, or null) receives the thread's
-// histogram runs.
+// Per-cell outputs of the read-only diagnostic pass; when o.hist is set the
+// thread's histogram runs go to the shared-memory counts hist_sm (bins
+// [hist_lo, hist_lo + hist_win)) and to the global counts hist_gl (the rest;
+// null when none).
 __device__ __forceinline__ void diag_write(const DiagOut& o, const CellDiag& g, int x, int y, int z,
-                                           int nx, int ny, int nz, uint32_t* hist, bool hist_global,
-                                           HistRun& run) {
+                                           int nx, int ny, int nz, uint32_t* hist_sm, int hist_lo,
+                                           int hist_win, uint32_t* hist_gl, HistRun& run) {
   const int64_t n = (int64_t)nx * ny * nz;
   const int64_t i = ((int64_t)z * ny + y) * nx + x;
   if (!in_bounds(x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z < nz)) return;
@@ -200,12 +203,12 @@ __device__ __forceinline__ void diag_write(const DiagOut& o, const CellDiag& g, 
     if (o.plane_axis == 1 && y == o.plane_index) o.plane[(int64_t)z * nx + x] = g.theta;
     if (o.plane_axis == 2 && z == o.plane_index) o.plane[(int64_t)y * nx + x] = g.theta;
   }
-  if (hist) {
+  if (o.hist) {
     int b = o.hist_bins;
     const float q = g.theta * o.hist_scale;
     if (q >= 0.f && q < (float)o.hist_bins) b = min((int)q, o.hist_bins - 1);
     const bool change = b != run.bin;
-    run.flush_if(hist, change, hist_global);
+    run.flush_if(hist_sm, hist_lo, hist_win, hist_gl, change);
     if (change) run.bin = b;
     run.n += 1u;
   }

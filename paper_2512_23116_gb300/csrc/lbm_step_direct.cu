@@ -32,7 +32,9 @@ k_step_direct(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, in
   Acc acc;
   acc.reset();
   HistRun run;
-  uint32_t* const hist = use_hist ? shist : dout.hist;
+  uint32_t* const hist_sm = use_hist ? shist : nullptr;
+  const int hist_win = use_hist ? dout.hist_bins + 1 : 0;
+  uint32_t* const hist_gl = use_hist ? nullptr : dout.hist;
   int cur = -1, hint = 0;
   for (int64_t t = tile_lo + blockIdx.x; t < tile_hi; t += gridDim.x) {
     const int ii = find_instance(insts, ninst, t, cur < 0 ? hint : cur);
@@ -107,7 +109,7 @@ k_step_direct(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, in
         }
       }
       if (MODE != MODE_STEP) acc.add(g, Fx, Fy, Fz, C);
-      if (MODE == MODE_DIAG) diag_write(dout, g, x, y, z, nx, ny, nz, hist, !use_hist, run);
+      if (MODE == MODE_DIAG) diag_write(dout, g, x, y, z, nx, ny, nz, hist_sm, 0, hist_win, hist_gl, run);
       x += dx;
       r += dr;
       if (x >= nx) {
@@ -121,7 +123,7 @@ k_step_direct(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, in
     if (cur >= 0)
       block_flush(acc, sa.partials + ((int64_t)cur * sa.grid + blockIdx.x) * kNP, blockDim.x, 0);
   }
-  if (MODE == MODE_DIAG && hist) run.flush(hist, !use_hist);
+  if (MODE == MODE_DIAG && dout.hist) run.flush(hist_sm, 0, hist_win, hist_gl);
   if (use_hist) {
     __syncthreads();
     for (int i = threadIdx.x; i <= dout.hist_bins; i += blockDim.x)

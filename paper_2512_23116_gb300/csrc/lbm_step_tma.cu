@@ -41,9 +41,11 @@
 // loads and collision arithmetic, no stores (a stage is reloaded as soon as
 // its consumers are done), the FP64 block partials of the step with
 // statistics, and the per-cell outputs (velocity, theta slices, theta
-// histogram in shared memory when the launch reserves room for it).
+// histogram: a window of bins that fits the room the launch reserves behind
+// the stages in shared memory, the rest in global counts).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <utility>
 
 #include "lbm_device.cuh"
@@ -505,12 +507,14 @@ struct CellLoop {
 
 // Per-cell outputs of the read-only statistics pass (MODE_DIAG) for a tile:
 // the outputs, the tile's first row and plane, the extents, the histogram
-// (shared memory or global counts).
+// (bins [hist_lo, hist_lo + hist_win) in shared memory, the rest in global
+// counts).
 struct DiagTile {
   DiagOut o;
   int y0, z, ny, nz;
-  uint32_t* hist;
-  bool hist_global;
+  uint32_t* hist_sm;
+  int hist_lo, hist_win;
+  uint32_t* hist_gl;
 };
 
 // Consumer thread of nct: collide cells r0 nx + x0, + nct, ... of a tile of
@@ -578,7 +582,7 @@ __device__ __forceinline__ void collide_tile(const CellLoop& cl, int ncell, cons
       }
     }
     if (MODE != MODE_STEP) acc.add(cd, Fx, Fy, Fz, cl.C);
-    if (MODE == MODE_DIAG) diag_write(dt.o, cd, x, dt.y0 + r, dt.z, nx, dt.ny, dt.nz, dt.hist, dt.hist_global, run);
+    if (MODE == MODE_DIAG) diag_write(dt.o, cd, x, dt.y0 + r, dt.z, nx, dt.ny, dt.nz, dt.hist_sm, dt.hist_lo, dt.hist_win, dt.hist_gl, run);
     x += cl.dx;
     r += cl.dr;
     if (x >= nx) {
@@ -592,7 +596,7 @@ template <typename T, bool ODD, int MODE, int SLOT>
 __global__ void __launch_bounds__(512, 1)
 k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64_t tile_hi,
            StatsArgs sa, int stages, int tile_bytes, uint32_t* __restrict__ err, long long wait_ns,
-           int withhold_first_load, DiagOut dout, int hist_smem) {
+           int withhold_first_load, DiagOut dout, int hist_smem, int hist_lo, int hist_win) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nconsumer_warps = (blockDim.x >> 5) - 1;
@@ -714,13 +718,20 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
   const int64_t first = tile_lo + blockIdx.x;
   const int64_t stride = gridDim.x;
   if (first >= tile_hi) return;
-  // MODE_DIAG: theta histogram in shared memory when the launch reserved room
-  // at byte hist_smem, else straight into the global counts
-  uint32_t* hist = nullptr;
+  // MODE_DIAG: theta histogram bins [hist_lo, hist_lo + hist_win) in shared
+  // memory when the launch reserved room at byte hist_smem, the others
+  // straight into the global counts
+  uint32_t* hist_sm = nullptr;
+  uint32_t* hist_gl = nullptr;
+  int lo = 0, win = 0;
   if (MODE == MODE_DIAG && dout.hist) {
-    hist = hist_smem > 0 ? reinterpret_cast<uint32_t*>(smem + hist_smem) : dout.hist;
-    if (hist_smem > 0)
-      for (int i = ctid; i <= dout.hist_bins; i += nct) hist[i] = 0u;
+    if (hist_smem > 0) {
+      hist_sm = reinterpret_cast<uint32_t*>(smem + hist_smem);
+      lo = min(max(hist_lo, 0), dout.hist_bins);
+      win = min(hist_win, dout.hist_bins + 1 - lo);
+      for (int i = ctid; i < win; i += nct) hist_sm[i] = 0u;
+    }
+    if (lo > 0 || win <= dout.hist_bins) hist_gl = dout.hist;
   }
   Acc acc;
   acc.reset();
@@ -784,7 +795,7 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
     const float Fy = __ldg(fy_of_z + g.z) + fy_const;
     const int ncell = g.rows * cl.nx;
     T* sbuf = reinterpret_cast<T*>(smem + kBarBytes + (size_t)st * tile_bytes);
-    const DiagTile dt{dout, g.y0, g.z, insts[w.ii].ny, insts[w.ii].nz, hist, hist_smem == 0};
+    const DiagTile dt{dout, g.y0, g.z, insts[w.ii].ny, insts[w.ii].nz, hist_sm, lo, win, hist_gl};
     if (smode == 1)
       collide_tile<T, ODD, MODE, 1, SLOT>(cl, ncell, fx, Fy, sbuf, fz_table, nct, acc, dt, run);
     else
@@ -798,11 +809,11 @@ k_step_tma(const InstDesc* __restrict__ insts, int ninst, int64_t tile_lo, int64
   }
   if (MODE != MODE_STEP && cur >= 0)
     block_flush(acc, sa.partials + ((int64_t)cur * sa.grid + blockIdx.x) * kNP, nct, 1);
-  if (MODE == MODE_DIAG && hist) run.flush(hist, hist_smem == 0);
-  if (MODE == MODE_DIAG && dout.hist && hist_smem > 0) {
+  if (MODE == MODE_DIAG && dout.hist) run.flush(hist_sm, lo, win, hist_gl);
+  if (MODE == MODE_DIAG && dout.hist && hist_sm) {
     named_sync(2, nct);
-    for (int i = ctid; i <= dout.hist_bins; i += nct)
-      if (hist[i]) atomicAdd(&dout.hist[i], hist[i]);
+    for (int i = ctid; i < win; i += nct)
+      if (hist_sm[i]) atomicAdd(&dout.hist[lo + i], hist_sm[i]);
   }
 }
 
@@ -810,7 +821,7 @@ template <typename T, bool ODD, int MODE, int SLOT>
 cudaError_t launch_tma_t(const LaunchArgs& la, cudaStream_t st) {
   return launch_kernel(k_step_tma<T, ODD, MODE, SLOT>, la.grid, la.threads, la.smem_bytes, st, la.insts,
                        la.ninst, la.tile_lo, la.tile_hi, la.sa, la.stages, la.tile_bytes_max, la.err,
-                       la.wait_ns, la.withhold_first_load, la.dout, la.hist_smem);
+                       la.wait_ns, la.withhold_first_load, la.dout, la.hist_smem, la.hist_lo, la.hist_win);
 }
 
 template <typename T, int SLOT>
@@ -899,6 +910,23 @@ cudaError_t launch_step_tma(const LaunchArgs& la, cudaStream_t st) {
     case 2: return dispatch_tma<__nv_bfloat16>(la, st);
   }
   return cudaErrorInvalidValue;
+}
+
+int tma_diag_smem_limit(int precision) {
+  // the per-block opt-in maximum less the pass's static shared memory (the
+  // block reduction's scratch)
+  cudaFuncAttributes a{};
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (precision) {
+    case 0: e = cudaFuncGetAttributes(&a, k_step_tma<float, false, MODE_DIAG, 0>); break;
+    case 1: e = cudaFuncGetAttributes(&a, k_step_tma<__half, false, MODE_DIAG, 0>); break;
+    case 2: e = cudaFuncGetAttributes(&a, k_step_tma<__nv_bfloat16, false, MODE_DIAG, 0>); break;
+  }
+  int dev = 0, optin = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return 0;
+  return std::min(kMaxDynSmem, optin - (int)a.sharedSizeBytes);
 }
 
 cudaError_t tma_prepare(int precision, int smem_bytes) {

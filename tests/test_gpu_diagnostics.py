@@ -82,10 +82,11 @@ def test_domain_stats_match_oracle(gpu_lib):
 
 # (kernel configuration, bins): the statistics pass of the direct kernel keeps
 # up to 12000 bins in shared memory, global counts above; the TMA kernel's
-# keeps them in shared memory behind its stages when they fit (runtime-stride
-# tiles of two 16-cell x-lines: 2.4 KB stages) and uses global counts summed
-# over the warp's lanes that flush the same bin when they do not (5760 B
-# slots: 214 KB of stages; or 60000 bins)
+# keeps a window of bins from that of theta = 3 nu0 up in shared memory behind
+# its stages, as many as fit (runtime-stride tiles of two 16-cell x-lines,
+# 2.4 KB stages: all of 4096, ~55,000 of 60,000; 5760 B slots, 214 KB of
+# stages: ~2000) and counts the rest in global memory, summed over the warp's
+# lanes that flush the same bin
 HIST_PATHS = [
     (dict(kernel=1, tile_rows=2, threads=256), 4096),
     (dict(kernel=1, tile_rows=2, threads=256), 20000),
@@ -123,6 +124,38 @@ def test_histogram_counts(gpu_lib, cfg, bins, steps):
     want = np.bincount(idx.ravel(), minlength=bins + 1)
     assert np.array_equal(h, want)
     assert np.count_nonzero(h[:bins]) > 10  # theta spread over many bins
+
+
+@pytest.mark.parametrize("bins,hist_max", [(4096, 0.01), (4096, 0.02), (16384, 0.04)])
+def test_histogram_split_between_shared_and_global_counts(gpu_lib, bins, hist_max):
+    """TMA statistics pass with 5760 B slots: the shared memory left behind
+    the 214 KB of stages holds a window of about 2000 bins from the bin of
+    theta = 3 nu0 up; the cells of this strongly sheared 16^3 LES (theta from
+    3 nu0 = 1.03e-3 to a few 1e-2) spread over more bins than that, so they
+    are counted on both sides of the window's end (and in the overflow bin),
+    and the counts are still exactly those of the pass's own per-cell theta."""
+    lbm = gpu_lib
+    n = 16
+    u = synthetic.random_solenoidal(n, seed=1, urms=0.05)
+    nu0 = oracle.derive_nu0(0.043, n, 2e3)
+    F0 = oracle.forcing_amplitude(0.2, 0.043, n)
+    p = lbm.make_params(n, nu0=nu0, cs=0.13, f0=F0, force_mode=lbm.LBM_FORCE_PAPER_SIN, hist_bins=bins,
+                        hist_max=hist_max, kernel=2, tile_rows=2, stages=2, threads=256)
+    with lbm.Lattice(p) as L:
+        assert L.config()["slot_bytes"] == 5760
+        L.init(lbm.LBM_INIT_VELOCITY, u=u)
+        L.step(10)
+        L.stats()
+        h = lbm.lbm_histogram(L.h, 0, bins)
+        th = L.fields()["theta"]
+    q = th.astype(np.float32) * np.float32(bins / hist_max)
+    idx = np.where(q < bins, np.floor(q), bins).astype(np.int64)
+    want = np.bincount(idx.ravel(), minlength=bins + 1)
+    used = np.nonzero(want)[0]
+    # no window of the shared memory left behind these stages (8 KB) spans it
+    assert used[-1] - used[0] > 8256 // 4, (used[0], used[-1])
+    assert int(h.sum()) == n ** 3
+    assert np.array_equal(h, want)
 
 
 def test_spectrum_single_mode(gpu_lib):
