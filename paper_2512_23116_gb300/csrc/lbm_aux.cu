@@ -197,31 +197,62 @@ __device__ __forceinline__ int shell_of(long long K) {
   return (int)(K > r * r + r ? r + 1 : r);
 }
 
+// shell_of for K < 2^24, where K is exact in FP32 and the FP32 square root is
+// within one of the integer root: no FP64 arithmetic (slow on this part).
+__device__ __forceinline__ int shell_of_small(int K) {
+  int r = (int)sqrtf((float)K);
+  while (r * r > K) --r;
+  while ((r + 1) * (r + 1) <= K) ++r;
+  return K > r * r + r ? r + 1 : r;
+}
+
+// A warp takes one (ky, kz) line of the half-spectrum at a time, lanes over kx
+// (no division per mode).  The shell does not decrease with kx, so the lanes
+// of one group of 32 modes that fall in one shell form a run: their FP32
+// energies are summed within the run (a segmented shuffle sum) and the run's
+// first lane adds the sum, scaled, to the block's FP64 shell total in shared
+// memory.
 __global__ void k_spec_bin(const float2* __restrict__ c, int nx, int ny, int nz, int kmax,
                            double* __restrict__ partials) {
   extern __shared__ double sh[];
   for (int s = threadIdx.x; s <= kmax; s += blockDim.x) sh[s] = 0.0;
   __syncthreads();
   const int nxh = nx / 2 + 1;
-  const int64_t n = (int64_t)nz * ny * nxh;
   const double ncell = (double)nx * ny * nz;
   const double scale = 0.5 / (ncell * ncell);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int kx = (int)(i % nxh);
-    const int64_t rest = i / nxh;
-    const int ky = (int)(rest % ny);
-    const int kz = (int)(rest / ny);
+  const int lane = threadIdx.x & 31;
+  const int64_t lines = (int64_t)ny * nz;
+  const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t l = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); l < lines; l += wstride) {
+    const int kz = (int)(l / ny), ky = (int)(l - (int64_t)kz * ny);
     const long long sy = ky <= ny / 2 ? ky : ky - ny;
     const long long sz = kz <= nz / 2 ? kz : kz - nz;
-    const long long K = (long long)kx * kx + sy * sy + sz * sz;
-    const int s = shell_of(K);
-    if (s > kmax) continue;
-    // the R2C half-spectrum holds each kx > 0 mode once for the pair (k, -k),
-    // except kx = 0 and the Nyquist plane kx = nx/2 (even nx)
-    const double wgt = (kx == 0 || (2 * kx == nx)) ? 1.0 : 2.0;
-    const float2 v = c[i];
-    atomicAdd(&sh[s], wgt * scale * ((double)v.x * v.x + (double)v.y * v.y));
+    const long long Kp = sy * sy + sz * sz;
+    const float2* row = c + l * nxh;
+    for (int x0 = 0; x0 < nxh; x0 += 32) {
+      const int kx = x0 + lane;
+      int s = kmax + 1;  // no contribution
+      float e = 0.f;
+      if (kx < nxh) {
+        const long long K = (long long)kx * kx + Kp;
+        const int sk = K < (1ll << 24) ? shell_of_small((int)K) : shell_of(K);
+        if (sk <= kmax) {
+          // the R2C half-spectrum holds each kx > 0 mode once for the pair
+          // (k, -k), except kx = 0 and the Nyquist plane kx = nx/2 (even nx)
+          const float2 v = row[kx];
+          s = sk;
+          e = ((kx == 0 || 2 * kx == nx) ? 1.f : 2.f) * (v.x * v.x + v.y * v.y);
+        }
+      }
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const float eo = __shfl_down_sync(0xffffffffu, e, off);
+        const int so = __shfl_down_sync(0xffffffffu, s, off);
+        if (lane + off < 32 && so == s) e += eo;
+      }
+      const int sp = __shfl_up_sync(0xffffffffu, s, 1);
+      if (s <= kmax && (lane == 0 || sp != s)) atomicAdd(&sh[s], scale * (double)e);
+    }
   }
   __syncthreads();
   for (int s = threadIdx.x; s <= kmax; s += blockDim.x)
@@ -285,67 +316,99 @@ __global__ void k_struct(const float* __restrict__ u, int nx, int ny, int nz, in
   }
 }
 
-// Structure functions of up to 24 separations in one launch (blockIdx.y =
-// separation): per block b and separation k, partials[(b * nr + k) * 6 + p - 1]
-// = sum over its cells and the three axes of d^p, d = u_a(x + r_k e_a) - u_a(x),
-// p = 1..6.  The powers and the running sums are FP32 (FP64 arithmetic is slow
-// on this part: with FP64 powers the 256^3 structure functions took 17 ms),
-// folded into FP64 totals every kFoldStruct cells; the block reduction is FP64.
+// Structure functions of up to 24 separations in one launch: blockIdx.y takes
+// a chunk of kStructChunk separations, a warp one x-line at a time (lanes over
+// x: no division per cell), so a cell's own velocity is read once per chunk
+// rather than once per separation.  Per block b and separation k,
+// partials[(b * nr + k) * 6 + p - 1] = sum over its cells and the three axes
+// of d^p, d = u_a(x + r_k e_a) - u_a(x), p = 1..6.  The powers and the running
+// sums are FP32 (FP64 arithmetic is slow on this part: with FP64 powers the
+// 256^3 structure functions took 17 ms), folded into FP64 totals every
+// kFoldStruct cells; the block reduction is FP64.
 constexpr int kFoldStruct = 32;
+constexpr int kStructChunk = 3;
 
-__global__ void k_struct_multi(const float* __restrict__ u, int nx, int ny, int nz, StructSeps seps, int nr,
+__global__ void __launch_bounds__(256, 2)
+k_struct_multi(const float* __restrict__ u, int nx, int ny, int nz, StructSeps seps, int nr,
                                double* __restrict__ partials) {
-  const int k = blockIdx.y;
+  const int k0 = blockIdx.y * kStructChunk;
+  const int kn = min(kStructChunk, nr - k0);
   const int64_t n = (int64_t)nx * ny * nz;
-  const int r = seps.r[k];
-  const int rx = r % nx, ry = r % ny, rz = r % nz;
-  double acc[6] = {0, 0, 0, 0, 0, 0};
-  float t[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  int rx[kStructChunk], ry[kStructChunk], rz[kStructChunk];
+#pragma unroll
+  for (int j = 0; j < kStructChunk; ++j) {
+    const int r = j < kn ? seps.r[k0 + j] : 0;
+    rx[j] = r % nx;
+    ry[j] = r % ny;
+    rz[j] = r % nz;
+  }
+  double acc[kStructChunk][6];
+  float t[kStructChunk][6];
+#pragma unroll
+  for (int j = 0; j < kStructChunk; ++j)
+#pragma unroll
+    for (int p = 0; p < 6; ++p) {
+      acc[j][p] = 0.0;
+      t[j][p] = 0.f;
+    }
   int cnt = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    int x, y, z;
-    cell_xyz(i, nx, ny, x, y, z);
-    const int xr = x + rx >= nx ? x + rx - nx : x + rx;
-    const int yr = y + ry >= ny ? y + ry - ny : y + ry;
-    const int zr = z + rz >= nz ? z + rz - nz : z + rz;
-    if (!in_bounds(xr >= 0 && xr < nx && yr >= 0 && yr < ny && zr >= 0 && zr < nz)) continue;
-    const float d3[3] = {u[((int64_t)z * ny + y) * nx + xr] - u[i],
-                         u[n + ((int64_t)z * ny + yr) * nx + x] - u[n + i],
-                         u[2 * n + ((int64_t)zr * ny + y) * nx + x] - u[2 * n + i]};
+  const int lane = threadIdx.x & 31;
+  const int64_t lines = (int64_t)ny * nz;
+  const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t l = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); l < lines; l += wstride) {
+    const int z = (int)(l / ny), y = (int)(l - (int64_t)z * ny);
+    const int64_t base = l * nx;
+    for (int x = lane; x < nx; x += 32) {
+      const float ux = u[base + x], uy = u[n + base + x], uz = u[2 * n + base + x];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      float q = d3[a];
+      for (int j = 0; j < kStructChunk; ++j) {
+        if (j >= kn) break;
+        const int xr = x + rx[j] >= nx ? x + rx[j] - nx : x + rx[j];
+        const int yr = y + ry[j] >= ny ? y + ry[j] - ny : y + ry[j];
+        const int zr = z + rz[j] >= nz ? z + rz[j] - nz : z + rz[j];
+        if (!in_bounds(xr >= 0 && xr < nx && yr >= 0 && yr < ny && zr >= 0 && zr < nz)) continue;
+        const float d3[3] = {u[base + xr] - ux, u[n + ((int64_t)z * ny + yr) * nx + x] - uy,
+                             u[2 * n + ((int64_t)zr * ny + y) * nx + x] - uz};
 #pragma unroll
-      for (int p = 0; p < 6; ++p) {
-        t[p] += q;
-        q *= d3[a];
+        for (int a = 0; a < 3; ++a) {
+          float q = d3[a];
+#pragma unroll
+          for (int p = 0; p < 6; ++p) {
+            t[j][p] += q;
+            q *= d3[a];
+          }
+        }
       }
-    }
-    if (++cnt == kFoldStruct) {
+      if (++cnt == kFoldStruct) {
 #pragma unroll
-      for (int p = 0; p < 6; ++p) {
-        acc[p] += (double)t[p];
-        t[p] = 0.f;
+        for (int j = 0; j < kStructChunk; ++j)
+#pragma unroll
+          for (int p = 0; p < 6; ++p) {
+            acc[j][p] += (double)t[j][p];
+            t[j][p] = 0.f;
+          }
+        cnt = 0;
       }
-      cnt = 0;
     }
   }
-#pragma unroll
-  for (int p = 0; p < 6; ++p) acc[p] += (double)t[p];
   __shared__ double red[32][6];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int p = 0; p < 6; ++p) {
-    double v = acc[p];
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    if (lane == 0) red[warp][p] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < 6) {
-    double v = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][threadIdx.x];
-    partials[((int64_t)blockIdx.x * nr + k) * 6 + threadIdx.x] = v;
+  for (int j = 0; j < kStructChunk; ++j) {
+    if (j >= kn) break;
+#pragma unroll
+    for (int p = 0; p < 6; ++p) {
+      double v = acc[j][p] + (double)t[j][p];
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if (lane == 0) red[warp][p] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+      double v = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][threadIdx.x];
+      partials[((int64_t)blockIdx.x * nr + k0 + j) * 6 + threadIdx.x] = v;
+    }
+    __syncthreads();
   }
 }
 
@@ -471,7 +534,9 @@ cudaError_t launch_struct_multi(const float* u, int nx, int ny, int nz, const in
   if (nr < 1 || nr > kMaxStructSeps) return cudaErrorInvalidValue;
   StructSeps seps{};
   for (int k = 0; k < nr; ++k) seps.r[k] = r[k];
-  return launch_kernel(k_struct_multi, dim3(blocks, nr), kAuxThreads, 0, st, u, nx, ny, nz, seps, nr, partials);
+  const int chunks = (nr + kStructChunk - 1) / kStructChunk;
+  return launch_kernel(k_struct_multi, dim3(blocks, chunks), kAuxThreads, 0, st, u, nx, ny, nz, seps, nr,
+                       partials);
 }
 
 cudaError_t launch_struct(const float* u, int nx, int ny, int nz, int r, double* partials,
