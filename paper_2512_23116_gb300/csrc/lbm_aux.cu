@@ -328,12 +328,15 @@ __global__ void k_struct(const float* __restrict__ u, int nx, int ny, int nz, in
 constexpr int kFoldStruct = 32;
 constexpr int kStructChunk = 3;
 
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(kAuxThreads, 2)
 k_struct_multi(const float* __restrict__ u, int nx, int ny, int nz, StructSeps seps, int nr,
-                               double* __restrict__ partials) {
+               double* __restrict__ partials) {
   const int k0 = blockIdx.y * kStructChunk;
   const int kn = min(kStructChunk, nr - k0);
   const int64_t n = (int64_t)nx * ny * nz;
+  // a chunk shorter than kStructChunk is padded with r = 0, whose increments
+  // are exactly zero: the cell loop has no branch per separation, so the
+  // loads of all separations are in flight together
   int rx[kStructChunk], ry[kStructChunk], rz[kStructChunk];
 #pragma unroll
   for (int j = 0; j < kStructChunk; ++j) {
@@ -342,13 +345,15 @@ k_struct_multi(const float* __restrict__ u, int nx, int ny, int nz, StructSeps s
     ry[j] = r % ny;
     rz[j] = r % nz;
   }
-  double acc[kStructChunk][6];
+  // FP64 totals of each thread in shared memory, leaving the registers to the
+  // loads in flight
+  __shared__ double tot[kStructChunk * 6][kAuxThreads];
   float t[kStructChunk][6];
 #pragma unroll
   for (int j = 0; j < kStructChunk; ++j)
 #pragma unroll
     for (int p = 0; p < 6; ++p) {
-      acc[j][p] = 0.0;
+      tot[j * 6 + p][threadIdx.x] = 0.0;
       t[j][p] = 0.f;
     }
   int cnt = 0;
@@ -362,7 +367,6 @@ k_struct_multi(const float* __restrict__ u, int nx, int ny, int nz, StructSeps s
       const float ux = u[base + x], uy = u[n + base + x], uz = u[2 * n + base + x];
 #pragma unroll
       for (int j = 0; j < kStructChunk; ++j) {
-        if (j >= kn) break;
         const int xr = x + rx[j] >= nx ? x + rx[j] - nx : x + rx[j];
         const int yr = y + ry[j] >= ny ? y + ry[j] - ny : y + ry[j];
         const int zr = z + rz[j] >= nz ? z + rz[j] - nz : z + rz[j];
@@ -384,21 +388,21 @@ k_struct_multi(const float* __restrict__ u, int nx, int ny, int nz, StructSeps s
         for (int j = 0; j < kStructChunk; ++j)
 #pragma unroll
           for (int p = 0; p < 6; ++p) {
-            acc[j][p] += (double)t[j][p];
+            tot[j * 6 + p][threadIdx.x] += (double)t[j][p];
             t[j][p] = 0.f;
           }
         cnt = 0;
       }
     }
   }
-  __shared__ double red[32][6];
+  __shared__ double red[kAuxThreads / 32][6];
   const int warp = threadIdx.x >> 5;
 #pragma unroll
   for (int j = 0; j < kStructChunk; ++j) {
     if (j >= kn) break;
 #pragma unroll
     for (int p = 0; p < 6; ++p) {
-      double v = acc[j][p] + (double)t[j][p];
+      double v = tot[j * 6 + p][threadIdx.x] + (double)t[j][p];
       for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
       if (lane == 0) red[warp][p] = v;
     }
