@@ -618,6 +618,38 @@ def les_c2_run(lbm, device, stream, n=100, steps=20000, every=500, plane=50, spr
             "kernel": cfg}
 
 
+def stats_cost(lbm, device, stream, n, precision, C, config="", layout=0, reps=3):
+    """Cost of each statistics call on the n^3 lattice from the seeded random
+    field (the paper's forcing, nu0 from Re = 2e4, Smagorinsky constant C):
+    milliseconds of host wall time around each synchronous call, after one
+    step that makes the cached velocity stale, minus that step; the first
+    call with the spectrum (the FFT's one-time setup) timed on its own."""
+    import torch
+    nu0 = U0 * n / RE
+    lat, _, cfg, _ = run_case(lbm, n, precision, C, nu0, 1, 1, device, stream, False, config=config,
+                              layout=layout)
+    W = {"plain": 0, "spectrum": lbm.LBM_STATS_SPECTRUM, "structure": lbm.LBM_STATS_STRUCTURE,
+         "spectrum_and_structure": lbm.LBM_STATS_SPECTRUM | lbm.LBM_STATS_STRUCTURE}
+
+    def wall(f, k=1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k):
+            f()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / k * 1e3
+
+    out = {"n": n, "precision": precision, "C": C, "kernel": cfg,
+           "first_spectrum_call_ms": wall(lambda: lbm.lbm_stats(lat.h, 0, W["spectrum"]))}
+    step_ms = wall(lambda: (lbm.lbm_step(lat.h, 1), lat.sync()), reps)
+    out["step_ms"] = step_ms
+    for name, what in W.items():
+        out[f"{name}_ms"] = wall(lambda: (lbm.lbm_step(lat.h, 1), lbm.lbm_stats(lat.h, 0, what)), reps) - step_ms
+    out["theta_slice_ms"] = wall(lambda: lbm.lbm_get_theta_slice(lat.h, 0, 2, n // 2, lat.shapes[0]), reps)
+    lat.close()
+    return out
+
+
 def l2_copy_rate(device, stream, mbytes=76, reps=50, rounds=4):
     """GB/s (read + write bytes) of an in-place FP32 multiply over an
     L2-resident buffer of `mbytes` MB, graph-replayed, CUDA events on the
@@ -668,6 +700,8 @@ def main():
                     help="roofline sweep N in {128, 256, 512, 1024}, FP32 and FP16, with spectral error at 128^3")
     ap.add_argument("--precision-study", action="store_true",
                     help="FP16/BF16 storage against FP32 at 800^3 over 2000 steps (spectral error, stability)")
+    ap.add_argument("--stats-cost", action="store_true",
+                    help="cost of each statistics call at --n (--precision, --cs, --config, --layout)")
     ap.add_argument("--shape", default="",
                     help="nx,ny,nz of a non-cubic box for --only-step profiling runs")
     ap.add_argument("--layout", type=int, default=0, choices=[0, 1, 2],
@@ -703,6 +737,13 @@ def main():
         res = sweep(lbm, local, stream)
         if rank == 0:
             print(json.dumps({"sweep": res}), flush=True)
+        return 0
+    if args.stats_cost:
+        stream = torch.cuda.Stream(device=dev)
+        res = stats_cost(lbm, local, stream, args.n, args.precision, args.cs, config=args.config,
+                         layout=args.layout)
+        if rank == 0:
+            print(json.dumps({"stats_cost": res}), flush=True)
         return 0
     if args.precision_study:
         stream = torch.cuda.Stream(device=dev)
