@@ -363,27 +363,48 @@ k_struct_multi(const float* __restrict__ u, int nx, int ny, int nz, StructSeps s
   for (int64_t l = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); l < lines; l += wstride) {
     const int z = (int)(l / ny), y = (int)(l - (int64_t)z * ny);
     const int64_t base = l * nx;
-    for (int x = lane; x < nx; x += 32) {
-      const float ux = u[base + x], uy = u[n + base + x], uz = u[2 * n + base + x];
+    // two cells per lane and pass (x and x + 32; the second one weighted 0
+    // past the end of the line), so that twice the loads are in flight
+    for (int x0 = lane; x0 < nx; x0 += 64) {
+      const int x1 = x0 + 32 < nx ? x0 + 32 : x0;
+      const float w1 = x0 + 32 < nx ? 1.f : 0.f;
+      const int xs[2] = {x0, x1};
+      float own[2][3];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        own[h][0] = u[base + xs[h]];
+        own[h][1] = u[n + base + xs[h]];
+        own[h][2] = u[2 * n + base + xs[h]];
+      }
 #pragma unroll
       for (int j = 0; j < kStructChunk; ++j) {
-        const int xr = x + rx[j] >= nx ? x + rx[j] - nx : x + rx[j];
         const int yr = y + ry[j] >= ny ? y + ry[j] - ny : y + ry[j];
         const int zr = z + rz[j] >= nz ? z + rz[j] - nz : z + rz[j];
-        if (!in_bounds(xr >= 0 && xr < nx && yr >= 0 && yr < ny && zr >= 0 && zr < nz)) continue;
-        const float d3[3] = {u[base + xr] - ux, u[n + ((int64_t)z * ny + yr) * nx + x] - uy,
-                             u[2 * n + ((int64_t)zr * ny + y) * nx + x] - uz};
+        float d[2][3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          float q = d3[a];
-#pragma unroll
-          for (int p = 0; p < 6; ++p) {
-            t[j][p] += q;
-            q *= d3[a];
-          }
+        for (int h = 0; h < 2; ++h) {
+          const int x = xs[h];
+          const int xr = x + rx[j] >= nx ? x + rx[j] - nx : x + rx[j];
+          const bool ok = in_bounds(xr >= 0 && xr < nx && yr >= 0 && yr < ny && zr >= 0 && zr < nz);
+          const float m = ok ? (h ? w1 : 1.f) : 0.f;
+          d[h][0] = m * (u[base + (ok ? xr : x)] - own[h][0]);
+          d[h][1] = m * (u[n + ((int64_t)z * ny + (ok ? yr : y)) * nx + x] - own[h][1]);
+          d[h][2] = m * (u[2 * n + ((int64_t)(ok ? zr : z) * ny + y) * nx + x] - own[h][2]);
         }
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            float q = d[h][a];
+#pragma unroll
+            for (int p = 0; p < 6; ++p) {
+              t[j][p] += q;
+              q *= d[h][a];
+            }
+          }
       }
-      if (++cnt == kFoldStruct) {
+      cnt += 2;
+      if (cnt >= kFoldStruct) {
 #pragma unroll
         for (int j = 0; j < kStructChunk; ++j)
 #pragma unroll
