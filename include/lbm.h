@@ -327,7 +327,11 @@ int lbm_get_velocity(lbm_t h, int32_t inst, double* u);
 
 /* One plane of theta = tau_e - 1/2 (the K_t map of Sec. 4.1): axis 0, 1, 2 =
  * the plane x = index, y = index or z = index; host array of the plane's two
- * other extents (row-major, the faster axis last).  Synchronous. */
+ * other extents (row-major, the faster axis last).  Synchronous.  A z-plane
+ * reads that plane's cells only (x- and y-planes cut every tile: the whole
+ * lattice); non-finite values appear in the slice as such, the domain-wide
+ * check is lbm_stats'.  Errors: INVALID_ARG (null handle or output, instance,
+ * axis or index out of range), TIMEOUT, UNSTABLE (x- and y-planes), CUDA. */
 int lbm_get_theta_slice(lbm_t h, int32_t inst, int32_t axis, int32_t index, double* host);
 
 /* Device pointer and size in bytes of the population array of `inst`, for

@@ -471,6 +471,15 @@ int diag_pass(lbm_t h, int i, bool want_u, bool want_aux, int plane_axis, int pl
   LaunchArgs la = base_args(h);
   la.tile_lo = I.tile_begin;
   la.tile_hi = I.tile_end;
+  // a z-plane alone (no other output): only that plane's tiles (tiles run
+  // plane by plane), and no reduction of the block partials, which then
+  // cover the plane only
+  const bool plane_only = plane_axis == 2 && !want_u && !want_aux && !want_hist;
+  if (plane_only) {
+    const int64_t tpp = (I.p.ny + I.rows - 1) / I.rows;
+    la.tile_lo = I.tile_begin + (int64_t)plane_index * tpp;
+    la.tile_hi = la.tile_lo + tpp;
+  }
   la.odd = (h->t & 1) != 0;
   la.mode = MODE_DIAG;
   la.dout.u = want_u ? I.u : nullptr;
@@ -527,8 +536,9 @@ int diag_pass(lbm_t h, int i, bool want_u, bool want_aux, int plane_axis, int pl
     ld.sa.grid = ld.grid;
     CK(h, launch_step_direct(ld, h->stream));
   }
-  CK(h, launch_finish(h->d_partials, (int)h->inst.size(), grid, h->d_results, nullptr, nullptr, 0, h->d_err,
-                      h->stream));
+  if (!plane_only)
+    CK(h, launch_finish(h->d_partials, (int)h->inst.size(), grid, h->d_results, nullptr, nullptr, 0, h->d_err,
+                        h->stream));
   if (want_u) I.u_version = h->version;
   return LBM_OK;
 }

@@ -231,16 +231,40 @@ def test_series_batched_instances(gpu_lib):
     assert math.isclose(r1[0]["theta_mean"], 3 * 0.02, rel_tol=1e-6)
 
 
-def test_theta_slice(gpu_lib):
+@pytest.mark.parametrize("kind", KINDS)
+def test_theta_slice(gpu_lib, kind):
+    """Slices on every axis equal the read-only pass's theta field, bit for
+    bit; a z-plane is computed from that plane's tiles alone."""
     lbm = gpu_lib
-    gpu, _, _ = _les_case(lbm, n=16)
+    gpu, _, _ = _les_case(lbm, n=16, kind=kind)
     with gpu:
         gpu.step(6)
         th = gpu.fields()["theta"]
-        for axis, idx in ((0, 3), (1, 0), (2, 15)):
+        for axis, idx in ((0, 3), (1, 0), (2, 15), (2, 0), (2, 7)):
             s = gpu.theta_slice(axis, idx)
             want = {0: th[:, :, idx], 1: th[:, idx, :], 2: th[idx]}[axis]
-            assert np.array_equal(s, want)
+            assert np.array_equal(s, want), (axis, idx)
+
+
+def test_theta_slice_of_a_later_instance(gpu_lib):
+    """z-plane slices of the second and third instances of a batched handle
+    (whose tiles start after the first instance's) and an x-plane, against
+    each instance's theta field; tiles of 3 x-lines, so a plane's last tile
+    is ragged."""
+    lbm = gpu_lib
+    shapes = [(6, 10, 12), (9, 7, 20), (5, 11, 16)]  # (nz, ny, nx)
+    params = [lbm.make_params(nx, ny, nz, nu0=0.01, cs=0.13, kernel=2, tile_rows=3, stages=2, threads=256)
+              for (nz, ny, nx) in shapes]
+    with lbm.Lattice(params) as g:
+        for i in range(3):
+            g.init(lbm.LBM_INIT_TGV3D, amplitude=0.04 + 0.01 * i, inst=i)
+        g.step(5)
+        for i in (1, 2):
+            th = g.fields(inst=i)["theta"]
+            nz = shapes[i][0]
+            for idx in (0, nz // 2, nz - 1):
+                assert np.array_equal(g.theta_slice(2, idx, inst=i), th[idx]), (i, idx)
+            assert np.array_equal(g.theta_slice(0, 5, inst=i), th[:, :, 5]), i
 
 
 def test_nonfinite_state_is_reported_and_recoverable(gpu_lib):
