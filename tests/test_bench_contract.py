@@ -41,6 +41,14 @@ def test_traffic_figure_matches_its_digest():
     assert bench.traffic_per_update("0" * 16) is None
 
 
+def test_traffic_figure_is_of_the_current_kernel():
+    # the step kernel's sources hash to the digest of the committed capture,
+    # so the bench line carries the measured traffic (it reports null after a
+    # change to the kernel until the capture is taken again)
+    assert bench.traffic_per_update(bench.kernel_digest()) is not None
+    assert bench.traffic_per_update(bench.kernel_digest(), "fp16") is not None
+
+
 def _run_bench(args, env_extra=None):
     import json
     import subprocess
