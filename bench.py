@@ -274,8 +274,15 @@ def time_steps(lbm, lat, stream, steps, warmup, dist):
     return ms
 
 
+def config_of(cfg: dict) -> str:
+    """The --config string (kind, tile rows, stages, threads, tma_slots) that
+    reproduces a handle's kernel configuration (lbm_kernel_config)."""
+    slots = {0: 1, 2880: 2}.get(cfg["slot_bytes"], 0) if cfg["kind"] == 2 else 0
+    return f"{cfg['kind']},{cfg['tile_rows']},{cfg['stages']},{cfg['threads']},{slots}"
+
+
 def run_case(lbm, n, precision, C, nu0, steps, warmup, device, stream, dist, clocks=None,
-             config="", shape=None, row_align=0, layout=0, u_out=None):
+             config="", shape=None, row_align=0, layout=0, u_out=None, strain_mode=0):
     """Create, initialise from the library's seeded random field (u_out, when
     given, receives its FP32 velocity), time `steps` steps."""
     kind = rows = stages = threads = slots = 0
@@ -287,7 +294,7 @@ def run_case(lbm, n, precision, C, nu0, steps, warmup, device, stream, dist, clo
     p = lbm.make_params(nx, ny, nz, precision=precision, nu0=nu0, cs=C, f0=CF * U0 * U0 / nx,
                         force_mode=lbm.LBM_FORCE_PAPER_SIN, device=device, stream=stream.cuda_stream,
                         kernel=kind, tile_rows=rows, stages=stages, threads=threads, row_align=row_align,
-                        layout=layout, tma_slots=slots)
+                        layout=layout, tma_slots=slots, strain_mode=strain_mode)
     lat = lbm.Lattice(p)
     lat.init_random(seed=SEED, urms=URMS, k0=K0, u_out=u_out)
     if clocks is not None:
@@ -618,6 +625,28 @@ def les_c2_run(lbm, device, stream, n=100, steps=20000, every=500, plane=50, spr
             "kernel": cfg}
 
 
+def strain_mode_cost(lbm, device, stream, m, cfg_les, n, cfg_fp16, les_steps=2000, steps=40):
+    """The self-consistent strain evaluation (lbm_params.strain_mode = 1: the
+    local s_nu(|S|) in the strain formula, a closed form plus two Newton steps
+    per cell) against the explicit one (0), same kernel configuration: the
+    m^3 LES in FP32 (L2-resident, where per-cell arithmetic shows) and the
+    n^3 lattice with C = 0.13 in FP16 storage (HBM-bound)."""
+    out = {}
+    for tag, size, prec, cfg, k, w in ((f"{m}^3_les_fp32", m, 0, cfg_les, les_steps, 20),
+                                       (f"{n}^3_les_fp16_shifted", n, 1, cfg_fp16, steps, 3)):
+        ms = {}
+        for mode in (0, 1):
+            lat, t, _, st = run_case(lbm, size, prec, 0.13, U0 * size / RE, k, w, device, stream, False,
+                                     config=config_of(cfg), layout=cfg["layout"], strain_mode=mode)
+            lat.close()
+            ms[mode] = t
+            assert math.isfinite(st["E_k"])
+        out[tag] = {"MLUPS_strain_mode_0": size ** 3 * k / (ms[0] * 1e-3) / 1e6,
+                    "MLUPS_strain_mode_1": size ** 3 * k / (ms[1] * 1e-3) / 1e6,
+                    "time_ratio_1_over_0": ms[1] / ms[0], "steps": k, "kernel": cfg}
+    return out
+
+
 def stats_cost(lbm, device, stream, n, precision, C, config="", layout=0, reps=3):
     """Cost of each statistics call on the n^3 lattice from the seeded random
     field (the paper's forcing, nu0 from Re = 2e4, Smagorinsky constant C):
@@ -858,6 +887,8 @@ def main():
             "note": f"{l2_mb} MB lattice: L2-resident (129 MB L2); the roofline fraction is of the "
                     "L2-resident copy rate measured beside it",
             "kernel": cfg3, "theta_mean": st4["theta_mean"]}
+        guarded("NEXT4_strain_mode_cost", lambda: strain_mode_cost(lbm, local, stream, m, cfg3, n,
+                                                                    extra[f"{n}^3_fp16_shifted"]["kernel"]))
         guarded("C2_100^3_les_20000_steps_statistics_every_500", lambda: les_c2_run(lbm, local, stream))
         guarded("C4_batch48_les_fp32_5000_steps", lambda: batch_case(lbm, local, stream, 5000, 10))
         guarded("C3_800^3_storage_precision_2000_steps", lambda: precision_study(lbm, local, stream, n=n))
