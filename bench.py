@@ -625,6 +625,61 @@ def les_c2_run(lbm, device, stream, n=100, steps=20000, every=500, plane=50, spr
             "kernel": cfg}
 
 
+def les_stationary(lbm, device, stream, n=100, t0=1000, t_end=600, window=(200, 600), every=10, plane=50):
+    """The paper's 100^3 LES run to its statistically stationary state (Sec.
+    3.1, Sec. 4.1): Re = 2e4 (nu0 = U0 n / Re), C = 0.13, the paper's forcing
+    (U0 = 0.043, Cf = 0.2), from the Taylor-Green field of amplitude U0, t0 =
+    1000 steps, t_end t0 steps; every `every` t0 the domain statistics and a
+    theta slice at z = `plane`.  Reported: theta = tau_e - 1/2 over t / t0 in
+    `window` (the paper's interval) -- domain mean, 5th / 95th percentiles,
+    maximum, the slice's mean and maximum, each also over 3 nu0 -- beside the
+    values the paper prints for this run (context: the paper's numbers, not
+    a parity bar); the flow's window means (E_k, u_rms, K_t, the injection
+    <F.u> against the resolved and subgrid dissipation, Re_lambda, eta, L)
+    and the series over time."""
+    import torch
+    nu0 = U0 * n / RE
+    p = lbm.make_params(n, nu0=nu0, cs=0.13, f0=CF * U0 * U0 / n, force_mode=lbm.LBM_FORCE_PAPER_SIN,
+                        device=device, stream=stream.cuda_stream)
+    recs = []
+    with lbm.Lattice(p) as L:
+        L.init(lbm.LBM_INIT_TGV3D, amplitude=U0)
+        cfg = L.config()
+        torch.cuda.synchronize()
+        t_start = time.perf_counter()
+        for k in range(every, t_end + 1, every):
+            L.step(every * t0)
+            st = L.stats(what=lbm.LBM_STATS_SPECTRUM)
+            sl = L.theta_slice(2, plane)
+            recs.append({"t_over_t0": k, "theta_mean": st["theta_mean"], "theta_p05": st["theta_p05"],
+                         "theta_p50": st["theta_p50"], "theta_p95": st["theta_p95"],
+                         "theta_max": st["theta_max"], "slice_mean": float(sl.mean()),
+                         "slice_p95": float(np.quantile(sl, 0.95)), "slice_max": float(sl.max()),
+                         "E_k": st["E_k"], "u_rms": st["u_rms"], "Kt_mean": st["Kt_mean"],
+                         "inj": st["inj"], "eps0": st["eps0"], "eps_sgs": st["eps_sgs"],
+                         "Re_lambda": st["Re_lambda"], "eta": st["eta"], "L": st["L"]})
+        wall = time.perf_counter() - t_start
+    win = [r for r in recs if window[0] <= r["t_over_t0"] <= window[1]]
+    keys = ("theta_mean", "theta_p05", "theta_p50", "theta_p95", "theta_max", "slice_mean", "slice_p95",
+            "slice_max")
+    flow = {k: float(np.mean([r[k] for r in win]))
+            for k in ("E_k", "u_rms", "Kt_mean", "inj", "eps0", "eps_sgs", "Re_lambda", "eta", "L")}
+    flow["injection_over_dissipation"] = flow["inj"] / (flow["eps0"] + flow["eps_sgs"])
+    mean = {k: float(np.mean([r[k] for r in win])) for k in keys}
+    th0 = 3 * nu0
+    return {"n": n, "steps": t_end * t0, "t0_steps": t0, "window_t_over_t0": list(window), "C": 0.13,
+            "nu0": nu0, "theta_molecular_3nu0": th0, "wall_s": wall,
+            "MLUPS": n ** 3 * t_end * t0 / wall / 1e6, "kernel": cfg,
+            "window_mean": mean, "window_mean_over_3nu0": {k: v / th0 for k, v in mean.items()},
+            "window_mean_flow": flow,
+            "window_min_theta_p05": float(min(r["theta_p05"] for r in win)),
+            "window_max_theta_p95": float(max(r["theta_p95"] for r in win)),
+            "window_max_theta": float(max(r["theta_max"] for r in win)),
+            "paper_sec_4_1": {"theta_mean": 1.34e-3, "theta_mean_over_3nu0": 2.08, "theta_p05_above": 1.0e-3,
+                              "theta_p95_below": 1.82e-3, "slice_peaks_up_to": 3.7e-3},
+            "series": [{k: (float(f"{v:.6g}") if isinstance(v, float) else v) for k, v in r.items()} for r in recs]}
+
+
 def strain_mode_cost(lbm, device, stream, m, cfg_les, n, cfg_fp16, les_steps=2000, steps=40):
     """The self-consistent strain evaluation (lbm_params.strain_mode = 1: the
     local s_nu(|S|) in the strain formula, a closed form plus two Newton steps
@@ -729,6 +784,8 @@ def main():
                     help="roofline sweep N in {128, 256, 512, 1024}, FP32 and FP16, with spectral error at 128^3")
     ap.add_argument("--precision-study", action="store_true",
                     help="FP16/BF16 storage against FP32 at 800^3 over 2000 steps (spectral error, stability)")
+    ap.add_argument("--les-stationary", action="store_true",
+                    help="the paper's 100^3 LES from the Taylor-Green field to t/t0 = 600 (t0 = 1000 steps)")
     ap.add_argument("--stats-cost", action="store_true",
                     help="cost of each statistics call at --n (--precision, --cs, --config, --layout)")
     ap.add_argument("--shape", default="",
@@ -766,6 +823,12 @@ def main():
         res = sweep(lbm, local, stream)
         if rank == 0:
             print(json.dumps({"sweep": res}), flush=True)
+        return 0
+    if args.les_stationary:
+        stream = torch.cuda.Stream(device=dev)
+        res = les_stationary(lbm, local, stream)
+        if rank == 0:
+            print(json.dumps({"les_stationary": res}), flush=True)
         return 0
     if args.stats_cost:
         stream = torch.cuda.Stream(device=dev)
@@ -890,6 +953,7 @@ def main():
         guarded("NEXT4_strain_mode_cost", lambda: strain_mode_cost(lbm, local, stream, m, cfg3, n,
                                                                     extra[f"{n}^3_fp16_shifted"]["kernel"]))
         guarded("C2_100^3_les_20000_steps_statistics_every_500", lambda: les_c2_run(lbm, local, stream))
+        guarded("C2_stationary_100^3_les_tgv_600k_steps", lambda: les_stationary(lbm, local, stream))
         guarded("C4_batch48_les_fp32_5000_steps", lambda: batch_case(lbm, local, stream, 5000, 10))
         guarded("C3_800^3_storage_precision_2000_steps", lambda: precision_study(lbm, local, stream, n=n))
         guarded("NEXT3_c_sweep_128^3_Re5000", lambda: c_sweep(lbm, local, stream))
