@@ -117,15 +117,19 @@ __device__ __forceinline__ float strain_norm(float TT, float Qt, float nu0, floa
   const float b = 0.5f + 3.f * nu0;
   const float p2 = 2.f * TT;
   const float p = p2 > 1e-30f ? p2 * rsqrtf(p2) : 0.f;
-  const float xs = __fdividef(2.f * p, b + sqrtf(b * b + 12.f * C * p));
+  const float q = b * b + 12.f * C * p;  // >= b^2 >= 1/4
+  const float xs = __fdividef(2.f * p, b + q * rsqrtf(q));
   const float x2 = xs * xs + 2.f * Qt;
   float x = x2 > 1e-30f ? x2 * rsqrtf(x2) : 0.f;
+  // Newton on h(x) with h and h' both multiplied by w^3, w = b + 3 C x = 1/s_nu
+  // (> 0): one division per step
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
-    const float sv = __fdividef(1.f, b + 3.f * C * x);
-    const float h = x * x - p2 * sv * sv - 2.f * Qt;
-    const float dh = 2.f * x + 6.f * C * p2 * sv * sv * sv;
-    if (dh > 1e-30f) x -= __fdividef(h, dh);
+    const float w = fmaf(3.f * C, x, b);
+    const float w3 = w * w * w;
+    const float num = fmaf(x, x, -2.f * Qt) * w3 - p2 * w;
+    const float den = fmaf(2.f * x, w3, 6.f * C * p2);
+    if (den > 1e-30f) x -= __fdividef(num, den);
   }
   return x;
 }
